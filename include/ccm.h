@@ -1,0 +1,178 @@
+/*
+ * ccm.h -- C ABI of the GB300-native convergent cross mapping (CCM) library.
+ *
+ * What one call computes (paper Sect. 1, Sect. 2.1, Sect. 3.1, Sect. 3.2; the
+ * equations are the method's, as the paper takes them from Sugihara et al.
+ * 2012):
+ *
+ *   For every pair (j, i) = (library variable, target variable), embedding
+ *   dimension E, delay tau, library size L and realization k:
+ *     - shadow manifold of series j: M_j(m) = (s_j[t], s_j[t-tau], ...,
+ *       s_j[t-(E-1)tau]), t = m + (E-1)tau, m in [0, N_m), N_m = N-(E-1)tau
+ *       (Sect. 1: lagged embedding; Sect. 3.2: "lagged-coordinate vector");
+ *     - a random library of L distinct manifold points (Sect. 1: r random
+ *       subsamples of size L; Sect. 3.1).  Point m is chosen when its key
+ *       ((hi32(Philox4x64-10(ctr=(m, k, L, (j<<16)|(E<<8)|tau),
+ *       key=(seed, 0)).word0)) << 32 | m) is among the L smallest;
+ *     - for every manifold point m (all N_m points are queries) its E+1
+ *       nearest library points, m itself excluded, ordered by (squared FP32
+ *       distance, manifold index) (Sect. 3.2);
+ *     - simplex projection (Sect. 2.1): d_i the distances, u_i =
+ *       exp(-d_i/d_1) (the limit 1 for d_i = 0, else 0, when d_1 = 0),
+ *       w_i = u_i / sum u, Xhat(m) = sum_i w_i s_i[t_i];
+ *     - the skill rho = Pearson(s_i[t_m], Xhat(m)) over m (Sect. 2.1),
+ *       accumulated in FP64; NaN when either variance is zero.
+ *
+ * Precision: distances, selection, weights and predictions in FP32;
+ * rho moments in FP64.
+ *
+ * Output layout: rho[pair][E][tau][L][k], FP64, C order, where the axes index
+ * the arrays of ccm_problem in the order given.
+ *
+ * Ownership: the caller owns every buffer it passes.  A context owns the
+ * device memory of its plans; a plan copies the problem description at
+ * ccm_plan time, so the caller may free the ccm_problem arrays on return.
+ * No exception crosses this ABI; every entry point returns a ccm_status, and
+ * ccm_last_error() gives a thread-local message for the last failure.
+ *
+ * Threads: one context may be used from several host threads; a plan must
+ * not be run concurrently with itself.
+ */
+#ifndef CCM_GB300_H
+#define CCM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CCM_OK = 0,
+  CCM_PENDING = 1,        /* ccm_poll: the job has not finished yet */
+  CCM_EINVAL = -1,        /* invalid argument; nothing was run */
+  CCM_ENOMEM = -2,        /* device or host allocation failed */
+  CCM_ETOOLARGE = -3,     /* the job's device footprint exceeds the context budget */
+  CCM_ECUDA = -4,         /* a CUDA call failed; see ccm_last_error() */
+  CCM_ETIMEOUT = -5,      /* a bounded wait ran out */
+  CCM_ECANCELLED = -6,    /* the job was cancelled */
+  CCM_ENOTFOUND = -7      /* unknown ticket */
+} ccm_status;
+
+/* ccm_problem.flags */
+#define CCM_INPUT_ON_DEVICE  0x1u  /* series pointers given to ccm_run are device memory */
+#define CCM_OUTPUT_ON_DEVICE 0x2u  /* rho (and debug outputs) given to ccm_run are device memory */
+
+typedef struct {
+  int32_t n_series;        /* V >= 2 series, each of length n */
+  int64_t n;               /* series length N */
+  int32_t n_pairs;         /* number of (j, i) pairs */
+  const int32_t* pairs;    /* [n_pairs][2] = (library var j, target var i), 0 <= i, j < V, i != j */
+  int32_t n_E;
+  const int32_t* E;        /* [n_E], each 1..10 */
+  int32_t n_tau;
+  const int32_t* tau;      /* [n_tau], each >= 1, with N_m = n - (E-1)tau >= E+2 */
+  int32_t n_L;
+  const int64_t* L;        /* [n_L], each E+2 <= L <= N_m for every (E, tau) of the grid */
+  int32_t r;               /* realizations per (pair, E, tau, L) cell, >= 1 */
+  uint64_t seed;           /* library sampler seed */
+  uint32_t flags;          /* CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE */
+} ccm_problem;
+
+/* Optional per-unit outputs for checking (all device or all host, following
+ * CCM_OUTPUT_ON_DEVICE).  Units are ordered like rho.  Sizes: libraries
+ * sum over units of L int32; neighbours sum of N_m*(E+1) int32 (row m of a
+ * unit holds the E+1 neighbours of query m, nearest first); predictions sum
+ * of N_m float32.  ccm_plan_info gives the totals.  Any member may be NULL. */
+typedef struct {
+  int32_t* libraries;
+  int32_t* neighbours;
+  float* predictions;
+} ccm_debug_out;
+
+typedef struct {
+  int64_t n_units;            /* realizations = n_pairs*n_E*n_tau*n_L*r */
+  int64_t n_queries;          /* sum over units of N_m */
+  int64_t library_entries;    /* sum over units of L */
+  int64_t neighbour_entries;  /* sum over units of N_m*(E+1) */
+  int64_t n_work_items;       /* (unit, query tile) items of the fused kernel */
+  size_t device_bytes;        /* device footprint of the plan */
+  double pair_count;          /* query-library pairs = sum over units of N_m*L */
+  double flop_count;          /* 3E FP32 flops per pair, summed */
+} ccm_plan_info;
+
+typedef struct ccm_context ccm_context;
+typedef struct ccm_plan_s ccm_plan_t;
+
+/* Create a context on CUDA device `device` whose plans may hold at most
+ * `hbm_budget_bytes` of device memory in total (0 = 90% of the free memory at
+ * creation).  Starts the serving thread lazily on the first ccm_submit. */
+ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context** out);
+
+/* Cancel pending jobs, join the serving thread, free every plan's memory. */
+ccm_status ccm_context_destroy(ccm_context* ctx);
+
+/* Validate the problem, build the work list (units sorted by cost, split into
+ * query tiles), reserve device memory.  Returns CCM_EINVAL for an invalid
+ * problem and CCM_ETOOLARGE when the footprint exceeds the context budget. */
+ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out);
+
+ccm_status ccm_plan_destroy(ccm_plan_t* plan);
+
+ccm_status ccm_plan_get_info(const ccm_plan_t* plan, ccm_plan_info* info);
+
+/* Run the whole sweep: sampler, fused kNN + simplex + rho kernel (one
+ * persistent launch), replayed from a CUDA graph after the first call.
+ * series: [n_series][n] FP32 (host unless CCM_INPUT_ON_DEVICE); rho: FP64 as
+ * above (host unless CCM_OUTPUT_ON_DEVICE).  cuda_stream: a cudaStream_t, or
+ * NULL to run on the plan's own stream and block until done.  With a caller
+ * stream and device output the call is asynchronous; with host input or
+ * output it synchronises the stream before returning.  Host series are
+ * checked for non-finite values (CCM_EINVAL). */
+ccm_status ccm_run(ccm_plan_t* plan, const float* series, double* rho, void* cuda_stream);
+
+/* ccm_run plus optional per-unit outputs (dbg may be NULL). */
+ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho,
+                      const ccm_debug_out* dbg, void* cuda_stream);
+
+/* The plain comparator: one sampler launch and one naive kNN launch per
+ * realization (thread per query, library read from global memory, sorted
+ * insertion), same precision and same results.  It exists to measure the
+ * batched path against; rho/series placement as in ccm_run. */
+ccm_status ccm_run_plain(ccm_plan_t* plan, const float* series, double* rho, void* cuda_stream);
+
+/* Serving: queue a job (the context copies the series into pinned staging,
+ * so the caller may free it on return).  The serving thread admits queued
+ * jobs while their device footprints fit the free budget, batches admitted
+ * jobs' work items into shared persistent launches, and overlaps them on
+ * several streams.  CCM_ETOOLARGE if the footprint exceeds the whole budget. */
+ccm_status ccm_submit(ccm_context* ctx, const ccm_problem* prob, const float* series,
+                      uint64_t* ticket);
+
+/* Non-blocking when timeout_ms == 0, otherwise waits up to timeout_ms.
+ * CCM_OK: rho (host, layout as ccm_run) written and the ticket retired;
+ * CCM_PENDING: not done yet; CCM_ENOTFOUND: unknown or retired ticket;
+ * a negative status if the job failed or was cancelled (ticket retired). */
+ccm_status ccm_poll(ccm_context* ctx, uint64_t ticket, double* rho, int32_t timeout_ms);
+
+/* Cancel a queued job that has not been admitted yet (CCM_PENDING if it is
+ * already running; it then finishes normally). */
+ccm_status ccm_cancel(ccm_context* ctx, uint64_t ticket);
+
+/* Submit/admit/finish timestamps (seconds on the context's monotonic clock)
+ * of a finished job that has not been polled yet. */
+ccm_status ccm_job_times(ccm_context* ctx, uint64_t ticket, double* submit_s, double* start_s,
+                         double* finish_s);
+
+/* Thread-local message describing the last non-OK status on this thread. */
+const char* ccm_last_error(void);
+
+/* Library version string. */
+const char* ccm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCM_GB300_H */

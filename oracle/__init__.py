@@ -64,6 +64,10 @@ def _load():
             lib.oracle_predict.argtypes = [_F32P, _F32P, ctypes.c_int64, ctypes.c_int32,
                                            ctypes.c_int32, _I32P, _F64P]
             lib.oracle_predict.restype = ctypes.c_int
+            lib.oracle_query_subset.argtypes = [_F32P, _F32P, ctypes.c_int64, ctypes.c_int32,
+                                                ctypes.c_int32, _I32P, ctypes.c_int64, _I64P,
+                                                ctypes.c_int64, ctypes.c_int32, _I32P, _F64P]
+            lib.oracle_query_subset.restype = ctypes.c_int
             lib.oracle_pearson.argtypes = [_F64P, _F64P, ctypes.c_int64]
             lib.oracle_pearson.restype = ctypes.c_double
             lib.oracle_skill.argtypes = [_F32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -139,6 +143,23 @@ def predict(lib_s: np.ndarray, tgt_s: np.ndarray, E: int, tau: int,
     if rc != 0:
         raise ValueError("invalid prediction arguments")
     return out
+
+
+def query_subset(lib_s: np.ndarray, tgt_s: np.ndarray, E: int, tau: int, lib: np.ndarray,
+                 queries, select_fp64: bool = False):
+    """Neighbours [nq][E+1] and predictions [nq] of the listed query points only."""
+    lib_s = _c(lib_s, np.float32)
+    tgt_s = _c(tgt_s, np.float32)
+    lib = _c(lib, np.int32)
+    q = _c(queries, np.int64)
+    nbr = np.zeros((len(q), E + 1), np.int32)
+    xh = np.zeros(len(q), np.float64)
+    rc = _load().oracle_query_subset(_ptr(lib_s, _F32P), _ptr(tgt_s, _F32P), len(lib_s), int(E),
+                                     int(tau), _ptr(lib, _I32P), len(lib), _ptr(q, _I64P), len(q),
+                                     int(bool(select_fp64)), _ptr(nbr, _I32P), _ptr(xh, _F64P))
+    if rc != 0:
+        raise ValueError("invalid query subset arguments")
+    return nbr, xh
 
 
 def pearson(x: np.ndarray, y: np.ndarray) -> float:

@@ -138,24 +138,29 @@ double sqdist_fp64(const float* s, int32_t E, int32_t tau, int64_t a, int64_t b)
 // distance orders like distance.  Exclusion is by index: another point at
 // distance 0 stays eligible.
 // ---------------------------------------------------------------------------
+void query_neighbours(const float* s, int32_t E, int32_t tau, const int32_t* lib, int64_t L,
+                      int32_t select_fp64, int64_t m, std::vector<std::pair<double, int32_t>>* cand,
+                      int32_t* nbr_row) {
+  const int32_t kk = E + 1;
+  cand->clear();
+  for (int64_t q = 0; q < L; ++q) {
+    const int32_t l = lib[q];
+    if (l == m) continue;
+    const double d2 = select_fp64 ? sqdist_fp64(s, E, tau, m, l)
+                                  : (double)sqdist_fp32(s, E, tau, m, l);
+    cand->push_back(std::make_pair(d2, l));
+  }
+  std::partial_sort(cand->begin(), cand->begin() + kk, cand->end());
+  for (int32_t i = 0; i < kk; ++i) nbr_row[i] = (*cand)[(size_t)i].second;
+}
+
 void neighbours(const float* s, int64_t n, int32_t E, int32_t tau, const int32_t* lib,
                 int64_t L, int32_t select_fp64, int32_t* nbr) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
-  const int32_t kk = E + 1;
   std::vector<std::pair<double, int32_t>> cand;
   cand.reserve((size_t)L);
-  for (int64_t m = 0; m < n_m; ++m) {
-    cand.clear();
-    for (int64_t q = 0; q < L; ++q) {
-      const int32_t l = lib[q];
-      if (l == m) continue;
-      const double d2 = select_fp64 ? sqdist_fp64(s, E, tau, m, l)
-                                    : (double)sqdist_fp32(s, E, tau, m, l);
-      cand.push_back(std::make_pair(d2, l));
-    }
-    std::partial_sort(cand.begin(), cand.begin() + kk, cand.end());
-    for (int32_t i = 0; i < kk; ++i) nbr[m * kk + i] = cand[(size_t)i].second;
-  }
+  for (int64_t m = 0; m < n_m; ++m)
+    query_neighbours(s, E, tau, lib, L, select_fp64, m, &cand, nbr + m * (E + 1));
 }
 
 // ---------------------------------------------------------------------------
@@ -164,31 +169,33 @@ void neighbours(const float* s, int64_t n, int32_t E, int32_t tau, const int32_t
 // x[t_i].  When d_1 = 0, u_i is the limit of exp(-d_i/d_1) as d_1 -> 0+:
 // 1 for d_i = 0 and 0 otherwise.
 // ---------------------------------------------------------------------------
+double query_predict(const float* lib_s, const float* tgt_s, int32_t E, int32_t tau,
+                     const int32_t* nbr_row, int64_t m) {
+  const int32_t kk = E + 1;
+  std::vector<double> d((size_t)kk), u((size_t)kk);
+  for (int32_t i = 0; i < kk; ++i) d[(size_t)i] = std::sqrt(sqdist_fp64(lib_s, E, tau, m, nbr_row[i]));
+  double d1 = d[0];
+  for (int32_t i = 1; i < kk; ++i) d1 = std::min(d1, d[(size_t)i]);
+  double usum = 0.0;
+  for (int32_t i = 0; i < kk; ++i) {
+    if (d1 > 0.0)
+      u[(size_t)i] = std::exp(-d[(size_t)i] / d1);
+    else
+      u[(size_t)i] = (d[(size_t)i] == 0.0) ? 1.0 : 0.0;
+    usum += u[(size_t)i];
+  }
+  double acc = 0.0;
+  for (int32_t i = 0; i < kk; ++i) {
+    const int64_t t_i = nbr_row[i] + (int64_t)(E - 1) * tau;
+    acc += (u[(size_t)i] / usum) * (double)tgt_s[t_i];
+  }
+  return acc;
+}
+
 void predict(const float* lib_s, const float* tgt_s, int64_t n, int32_t E, int32_t tau,
              const int32_t* nbr, double* xhat) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
-  const int32_t kk = E + 1;
-  std::vector<double> d((size_t)kk), u((size_t)kk);
-  for (int64_t m = 0; m < n_m; ++m) {
-    for (int32_t i = 0; i < kk; ++i)
-      d[(size_t)i] = std::sqrt(sqdist_fp64(lib_s, E, tau, m, nbr[m * kk + i]));
-    double d1 = d[0];
-    for (int32_t i = 1; i < kk; ++i) d1 = std::min(d1, d[(size_t)i]);
-    double usum = 0.0;
-    for (int32_t i = 0; i < kk; ++i) {
-      if (d1 > 0.0)
-        u[(size_t)i] = std::exp(-d[(size_t)i] / d1);
-      else
-        u[(size_t)i] = (d[(size_t)i] == 0.0) ? 1.0 : 0.0;
-      usum += u[(size_t)i];
-    }
-    double acc = 0.0;
-    for (int32_t i = 0; i < kk; ++i) {
-      const int64_t t_i = nbr[m * kk + i] + (int64_t)(E - 1) * tau;
-      acc += (u[(size_t)i] / usum) * (double)tgt_s[t_i];
-    }
-    xhat[m] = acc;
-  }
+  for (int64_t m = 0; m < n_m; ++m) xhat[m] = query_predict(lib_s, tgt_s, E, tau, nbr + m * (E + 1), m);
 }
 
 // Pearson correlation, two passes in FP64; NaN when either variance is 0.
@@ -246,6 +253,23 @@ int oracle_predict(const float* lib_s, const float* tgt_s, int64_t n, int32_t E,
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
   if (E < 1 || tau < 1 || n_m < 1) return -1;
   predict(lib_s, tgt_s, n, E, tau, nbr, xhat_out);
+  return 0;
+}
+
+// Neighbours [nq][E+1] and predictions [nq] of the listed query points only
+// (for checking sampled outputs of large problems).
+int oracle_query_subset(const float* lib_s, const float* tgt_s, int64_t n, int32_t E, int32_t tau,
+                        const int32_t* lib, int64_t L, const int64_t* queries, int64_t nq,
+                        int32_t select_fp64, int32_t* nbr_out, double* xhat_out) {
+  const int64_t n_m = n - (int64_t)(E - 1) * tau;
+  if (E < 1 || tau < 1 || n_m < 1 || L < E + 2 || L > n_m) return -1;
+  std::vector<std::pair<double, int32_t>> cand;
+  cand.reserve((size_t)L);
+  for (int64_t q = 0; q < nq; ++q) {
+    if (queries[q] < 0 || queries[q] >= n_m) return -1;
+    query_neighbours(lib_s, E, tau, lib, L, select_fp64, queries[q], &cand, nbr_out + q * (E + 1));
+    xhat_out[q] = query_predict(lib_s, tgt_s, E, tau, nbr_out + q * (E + 1), queries[q]);
+  }
   return 0;
 }
 

@@ -1,0 +1,85 @@
+// Internal declarations shared by the CUDA kernels and the host runtime of the
+// CCM library (not part of the public ABI, see include/ccm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccm {
+
+constexpr int kMaxE = 10;
+
+// One realization ("unit"): pair (j, i), E, tau, L, realization k of one job.
+struct UnitDesc {
+  int64_t series_off;   // element offset of the job's series block [V][n]
+  int64_t n;            // series length of the job
+  int64_t lib_off;      // offset of this unit's library in the library buffer
+  int64_t part_off;     // first partial-moment slot (one per query tile)
+  int64_t q_off;        // first query of this unit in the concatenated debug outputs
+  int64_t nbr_off;      // first neighbour entry in the concatenated debug outputs
+  int64_t out_idx;      // index of this unit's rho in the rho buffer
+  uint64_t seed;        // library sampler seed of the job
+  int32_t j, i;         // library variable, target variable
+  int32_t E, tau;
+  int32_t L, k;
+  int32_t n_m;          // manifold points = queries
+  int32_t n_tiles;      // query tiles of the fused kernel
+};
+
+// One work item of the fused kernel: a query tile of a unit.
+struct WorkItem {
+  int32_t unit;
+  int32_t tile;
+};
+
+// Sampler: one CTA per unit.
+struct SamplerParams {
+  const UnitDesc* units;
+  int32_t* lib;           // library buffer (sum of L)
+  int32_t* dbg_lib;       // optional: libraries again, concatenated in unit order
+  const int64_t* dbg_lib_off;  // per-unit offsets into dbg_lib (NULL when dbg_lib is NULL)
+  int32_t* err;           // error flag (set, never cleared, by the kernels)
+};
+
+// Fused kNN + simplex + moments: persistent, one work item at a time.
+struct KnnParams {
+  const float* series;    // device series blocks
+  const UnitDesc* units;
+  const WorkItem* items;
+  int64_t n_items;
+  const int32_t* lib;
+  double* partials;       // 6 doubles per query tile
+  uint32_t* unit_done;    // per-unit tile counters (reset by the unit's last tile)
+  uint32_t* item_counter; // dynamic scheduling counter (zeroed before each launch)
+  double* rho;            // output (device), indexed by UnitDesc::out_idx
+  int32_t* dbg_nbr;       // optional [sum N_m][E+1]
+  float* dbg_xhat;        // optional [sum N_m]
+  int32_t* err;
+  int32_t persistent;     // 1: CTAs pull items from item_counter; 0: item = blockIdx.x
+};
+
+// Error flag values written by kernels.
+constexpr int32_t kErrBadUnit = 1;
+constexpr int32_t kErrSampler = 2;
+
+// Sampler (sampler.cu).
+constexpr int kSamplerThreads = 512;
+constexpr int kSamplerSmemKeys = 40960;   // keys kept in shared memory up to this N_m
+cudaError_t sampler_prepare();
+cudaError_t launch_sampler(const SamplerParams& p, int64_t first_unit, int64_t count,
+                           int max_nm, cudaStream_t s);
+
+// Fused kernel (knn_fused.cu).
+int knn_block_threads();
+int knn_queries_per_thread();
+size_t knn_smem_bytes(int emin, int emax);
+cudaError_t knn_prepare();
+cudaError_t knn_occupancy(int emin, int emax, int* ctas_per_sm);
+cudaError_t launch_knn(const KnnParams& p, int emin, int emax, int grid, cudaStream_t s);
+
+// Plain comparator (plain.cu): one realization per call.
+cudaError_t launch_plain_unit(const float* series, const UnitDesc* unit_dev, const UnitDesc& unit,
+                              const int32_t* lib, float* xhat_scratch, double* rho_out,
+                              int32_t* dbg_nbr, float* dbg_xhat, int32_t* err, cudaStream_t s);
+
+}  // namespace ccm

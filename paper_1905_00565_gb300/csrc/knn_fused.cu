@@ -1,0 +1,445 @@
+// Fused nearest-neighbour search + simplex projection + skill moments.
+//
+// For one query tile of one realization (paper Sect. 3.2: "finding the E+1
+// nearest neighbors for every lagged-coordinate vector", the step the paper
+// names as the most time-consuming), every query point of the shadow manifold
+// M_j is compared with every library point; the E+1 nearest (itself
+// excluded) give the simplex prediction of the target variable (Sect. 2.1),
+// and the tile's FP64 moments of (observed, predicted) are merged per
+// realization into the Pearson skill (Sect. 2.1).
+//
+// Design (GB300, FP32 on the CUDA cores; E <= 10 is not a dense contraction):
+//  * persistent CTAs pull (realization, query tile) items, sorted by cost,
+//    from an atomic counter;
+//  * each thread owns two queries whose coordinates sit packed in f32x2
+//    registers, so one sub.f32x2 + fma.f32x2 pair advances both queries;
+//  * the library is staged through shared memory tile by tile, each
+//    coordinate stored twice ({c, c}) so that a broadcast 128-bit load feeds
+//    the packed operations directly;
+//  * squared distances are accumulated in coordinate order (first term a
+//    rounded product, then one fused multiply-add per coordinate), the same
+//    rounding sequence the FP32 selection is defined by;
+//  * each query keeps its E+2 best (squared distance, index) in registers,
+//    sorted; candidates under the current threshold are appended to a small
+//    per-query buffer in shared memory and merged, warp-wide, when a buffer
+//    runs full, so a rare insertion in one lane does not stall the warp for a
+//    full sorted insertion every time;
+//  * the library is visited in ascending manifold index, so a strict "<"
+//    during insertion keeps equal distances in index order;
+//  * the epilogue drops the query itself, forms u_i = exp(-d_i/d_1), the
+//    prediction, and FP64 moments; the last tile of a realization to finish
+//    merges the tiles' moments in tile order (Chan et al. pairwise update),
+//    so rho does not depend on the schedule.
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include "ccm_internal.h"
+
+namespace ccm {
+namespace {
+
+using u64 = unsigned long long;
+
+constexpr int kThreads = 256;             // threads per CTA
+constexpr int kQ = 2;                     // queries per thread (one packed f32x2 pair)
+constexpr int kQT = kThreads * kQ;        // queries per tile
+constexpr int kBuf = 8;                   // pending candidates per query
+constexpr int kCoordBytes = 64 * 1024;    // shared memory for one library tile
+constexpr int kBufBytes = kBuf * kQ * kThreads * 8;
+constexpr int kSmemBytes = kCoordBytes + kBufBytes;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int E>
+struct TileShape {
+  static constexpr int EP = E + (E & 1);                              // coordinates padded to even
+  static constexpr int LT = (kCoordBytes / (EP * 8 + 4)) & ~63;       // library points per tile
+  static_assert(LT >= 64, "tile too small");
+};
+
+__device__ __forceinline__ u64 pack2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(u64 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Squared distances of the two packed queries to one library point whose
+// duplicated coordinates start at `c` (16-byte aligned, EP entries).
+template <int E>
+__device__ __forceinline__ u64 sqdist2(const u64 (&qc)[E], const u64* c) {
+  const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(c);
+  u64 acc = 0;
+#pragma unroll
+  for (int e = 0; e < E; e += 2) {
+    const ulonglong2 v = c2[e / 2];
+    const u64 d0 = sub2(qc[e], v.x);
+    acc = (e == 0) ? mul2(d0, d0) : fma2(d0, d0, acc);
+    if (e + 1 < E) {
+      const u64 d1 = sub2(qc[e + 1], v.y);
+      acc = fma2(d1, d1, acc);
+    }
+  }
+  return acc;
+}
+
+// Insert (x, lx) into the ascending list kd[0..K), keeping entries that are
+// equal to x ahead of it (they arrived earlier, with smaller index).  A no-op
+// when x is not below kd[K-1].
+template <int K>
+__device__ __forceinline__ void insert_sorted(float (&kd)[K], int (&kl)[K], float x, int lx) {
+  bool below[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) below[s] = x < kd[s];
+#pragma unroll
+  for (int s = K - 1; s > 0; --s) {
+    kd[s] = below[s - 1] ? kd[s - 1] : (below[s] ? x : kd[s]);
+    kl[s] = below[s - 1] ? kl[s - 1] : (below[s] ? lx : kl[s]);
+  }
+  kd[0] = below[0] ? x : kd[0];
+  kl[0] = below[0] ? lx : kl[0];
+}
+
+// Deterministic block sum of three doubles; every thread gets the totals.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(kFull, a, o);
+    b += __shfl_xor_sync(kFull, b, o);
+    c += __shfl_xor_sync(kFull, c, o);
+  }
+  if (lane == 0) {
+    s_red[3 * warp + 0] = a;
+    s_red[3 * warp + 1] = b;
+    s_red[3 * warp + 2] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0, tc = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      ta += s_red[3 * w + 0];
+      tb += s_red[3 * w + 1];
+      tc += s_red[3 * w + 2];
+    }
+    s_red[3 * (kThreads / 32) + 0] = ta;
+    s_red[3 * (kThreads / 32) + 1] = tb;
+    s_red[3 * (kThreads / 32) + 2] = tc;
+  }
+  __syncthreads();
+  a = s_red[3 * (kThreads / 32) + 0];
+  b = s_red[3 * (kThreads / 32) + 1];
+  c = s_red[3 * (kThreads / 32) + 2];
+  __syncthreads();
+}
+
+template <int E>
+__device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, int tile,
+                             unsigned char* smem, double* s_red, int* s_last) {
+  constexpr int K = E + 2;
+  constexpr int EP = TileShape<E>::EP;
+  constexpr int LT = TileShape<E>::LT;
+  u64* s_coord = reinterpret_cast<u64*>(smem);                              // [LT][EP]
+  int32_t* s_lidx = reinterpret_cast<int32_t*>(smem + (size_t)LT * EP * 8);  // [LT]
+  int2* s_buf = reinterpret_cast<int2*>(smem + kCoordBytes);                // [kBuf][kQ][kThreads]
+
+  const int tid = threadIdx.x;
+  const int n_m = u.n_m, L = u.L, tau = u.tau;
+  const int off = (E - 1) * tau;
+  const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
+  const float* si = p.series + u.series_off + (int64_t)u.i * u.n;
+  const int32_t* lib = p.lib + u.lib_off;
+
+  int m[kQ];
+  bool valid[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    m[q] = tile * kQT + q * kThreads + tid;
+    valid[q] = m[q] < n_m;
+    if (!valid[q]) m[q] = n_m - 1;
+  }
+  u64 qc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) qc[e] = pack2(sj[m[0] + off - e * tau], sj[m[1] + off - e * tau]);
+
+  float kd[kQ][K];
+  int kl[kQ][K];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q)
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      kd[q][s] = INFINITY;
+      kl[q][s] = -1;
+    }
+  int cnt[kQ] = {0, 0};
+
+  auto merge_all = [&]() {
+    int mx = max(cnt[0], cnt[1]);
+    mx = (int)__reduce_max_sync(kFull, (unsigned)mx);
+    for (int b = 0; b < mx; ++b) {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        if (b < cnt[q]) {
+          const int2 v = s_buf[(b * kQ + q) * kThreads + tid];
+          insert_sorted<K>(kd[q], kl[q], __int_as_float(v.x), v.y);
+        }
+      }
+    }
+    cnt[0] = 0;
+    cnt[1] = 0;
+  };
+
+  for (int t0 = 0; t0 < L; t0 += LT) {
+    const int nt = min(LT, L - t0);
+    const int ntp = (nt + 1) & ~1;
+    __syncthreads();  // the previous tile has been consumed
+    for (int a = tid; a < ntp; a += kThreads) {
+      if (a < nt) {
+        const int l = lib[t0 + a];
+        s_lidx[a] = l;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const float c = sj[l + off - e * tau];
+          s_coord[a * EP + e] = pack2(c, c);
+        }
+      } else {  // sentinel point: infinite distance, never selected
+        s_lidx[a] = 0x7fffffff;
+#pragma unroll
+        for (int e = 0; e < E; ++e) s_coord[a * EP + e] = pack2(INFINITY, INFINITY);
+      }
+      if (EP > E) s_coord[a * EP + E] = 0ull;
+    }
+    __syncthreads();
+
+#pragma unroll 1
+    for (int a = 0; a < ntp; a += 2) {
+      const u64 r0 = sqdist2<E>(qc, s_coord + (size_t)a * EP);
+      const u64 r1 = sqdist2<E>(qc, s_coord + (size_t)(a + 1) * EP);
+      float d00, d10, d01, d11;  // d[query][point]
+      unpack2(r0, d00, d10);
+      unpack2(r1, d01, d11);
+      const float th0 = kd[0][K - 1], th1 = kd[1][K - 1];
+      const bool pass = (d00 < th0) | (d01 < th0) | (d10 < th1) | (d11 < th1);
+      if (__any_sync(kFull, pass)) {
+        const int l0 = s_lidx[a], l1 = s_lidx[a + 1];
+        if (d00 < th0) { s_buf[(cnt[0] * kQ + 0) * kThreads + tid] = make_int2(__float_as_int(d00), l0); ++cnt[0]; }
+        if (d01 < th0) { s_buf[(cnt[0] * kQ + 0) * kThreads + tid] = make_int2(__float_as_int(d01), l1); ++cnt[0]; }
+        if (d10 < th1) { s_buf[(cnt[1] * kQ + 1) * kThreads + tid] = make_int2(__float_as_int(d10), l0); ++cnt[1]; }
+        if (d11 < th1) { s_buf[(cnt[1] * kQ + 1) * kThreads + tid] = make_int2(__float_as_int(d11), l1); ++cnt[1]; }
+        const bool need = (cnt[0] > kBuf - 2) | (cnt[1] > kBuf - 2);
+        if (__any_sync(kFull, need)) merge_all();
+      }
+    }
+  }
+  merge_all();
+
+  // Epilogue: drop the query itself, simplex weights, prediction, moments.
+  double xo[kQ], xp[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    int self = K;
+#pragma unroll
+    for (int s = 0; s < K; ++s) self = (kl[q][s] == m[q] && self == K) ? s : self;
+    float dd[E + 1];
+    int nb[E + 1];
+#pragma unroll
+    for (int s = 0; s <= E; ++s) {
+      dd[s] = (s < self) ? kd[q][s] : kd[q][s + 1];
+      nb[s] = (s < self) ? kl[q][s] : kl[q][s + 1];
+    }
+    const float d1 = sqrtf(dd[0]);
+    float usum = 0.f, acc = 0.f;
+#pragma unroll
+    for (int s = 0; s <= E; ++s) {
+      const float di = sqrtf(dd[s]);
+      const float ui = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
+      usum += ui;
+      // an unfilled slot (only possible with non-finite device input) reads in bounds
+      const int nbc = min(max(nb[s], 0), n_m - 1);
+      acc = fmaf(ui, si[nbc + off], acc);
+    }
+    const float xhat = acc / usum;
+    xo[q] = valid[q] ? (double)si[m[q] + off] : 0.0;
+    xp[q] = valid[q] ? (double)xhat : 0.0;
+    if (valid[q]) {
+      if (p.dbg_xhat) p.dbg_xhat[u.q_off + m[q]] = xhat;
+      if (p.dbg_nbr) {
+#pragma unroll
+        for (int s = 0; s <= E; ++s) p.dbg_nbr[u.nbr_off + (int64_t)m[q] * (E + 1) + s] = nb[s];
+      }
+    }
+  }
+
+  // Tile moments, two passes over the registers.
+  double n = 0.0, sx = 0.0, sy = 0.0;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    n += valid[q] ? 1.0 : 0.0;
+    sx += xo[q];
+    sy += xp[q];
+  }
+  block_sum3(n, sx, sy, s_red);
+  const double mx = sx / n, my = sy / n;
+  double sxx = 0.0, syy = 0.0, sxy = 0.0;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    if (valid[q]) {
+      const double a = xo[q] - mx, b = xp[q] - my;
+      sxx += a * a;
+      syy += b * b;
+      sxy += a * b;
+    }
+  }
+  block_sum3(sxx, syy, sxy, s_red);
+
+  if (tid == 0) {
+    double* part = p.partials + 6 * (u.part_off + tile);
+    part[0] = n;
+    part[1] = mx;
+    part[2] = my;
+    part[3] = sxx;
+    part[4] = syy;
+    part[5] = sxy;
+    __threadfence();
+    const unsigned prev = atomicAdd(&p.unit_done[unit], 1u);
+    *s_last = (prev == (unsigned)(u.n_tiles - 1)) ? 1 : 0;
+    if (*s_last) {
+      __threadfence();
+      const double* base = p.partials + 6 * u.part_off;
+      double N = __ldcg(base + 0), MX = __ldcg(base + 1), MY = __ldcg(base + 2);
+      double SXX = __ldcg(base + 3), SYY = __ldcg(base + 4), SXY = __ldcg(base + 5);
+      for (int t = 1; t < u.n_tiles; ++t) {
+        const double* pt = base + 6 * t;
+        const double nb = __ldcg(pt + 0), mxb = __ldcg(pt + 1), myb = __ldcg(pt + 2);
+        const double tot = N + nb;
+        const double dx = mxb - MX, dy = myb - MY;
+        const double f = N * nb / tot;
+        SXX += __ldcg(pt + 3) + dx * dx * f;
+        SYY += __ldcg(pt + 4) + dy * dy * f;
+        SXY += __ldcg(pt + 5) + dx * dy * f;
+        MX += dx * nb / tot;
+        MY += dy * nb / tot;
+        N = tot;
+      }
+      p.rho[u.out_idx] = (SXX > 0.0 && SYY > 0.0) ? SXY / sqrt(SXX * SYY) : nan("");
+      p.unit_done[unit] = 0u;  // ready for the next run
+    }
+  }
+  __syncthreads();
+}
+
+template <int EMIN, int EMAX>
+__device__ __forceinline__ bool dispatch(int E, const KnnParams& p, const UnitDesc& u, int unit,
+                                         int tile, unsigned char* smem, double* s_red,
+                                         int* s_last) {
+  bool ok = false;
+#define CCM_CASE(EV)                                                    \
+  if constexpr (EV >= EMIN && EV <= EMAX) {                             \
+    if (E == EV) {                                                      \
+      process_tile<EV>(p, u, unit, tile, smem, s_red, s_last);          \
+      ok = true;                                                        \
+    }                                                                   \
+  }
+  CCM_CASE(1) CCM_CASE(2) CCM_CASE(3) CCM_CASE(4) CCM_CASE(5)
+  CCM_CASE(6) CCM_CASE(7) CCM_CASE(8) CCM_CASE(9) CCM_CASE(10)
+#undef CCM_CASE
+  return ok;
+}
+
+template <int EMIN, int EMAX>
+__global__ void __launch_bounds__(kThreads, 2) knn_fused_kernel(KnnParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double s_red[3 * (kThreads / 32) + 3];
+  __shared__ int s_item, s_last;
+  for (int64_t round = 0;; ++round) {
+    if (p.persistent) {
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(p.item_counter, 1u);
+      __syncthreads();
+    }
+    const int it = p.persistent ? s_item : (round == 0 ? (int)blockIdx.x : INT_MAX);
+    __syncthreads();
+    if ((int64_t)it >= p.n_items) break;
+    const WorkItem w = p.items[it];
+    const UnitDesc u = p.units[w.unit];
+    if (!dispatch<EMIN, EMAX>(u.E, p, u, w.unit, w.tile, smem, s_red, &s_last)) {
+      if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
+    }
+  }
+}
+
+template <int EMIN, int EMAX>
+cudaError_t launch_range(const KnnParams& p, int grid, cudaStream_t s) {
+  knn_fused_kernel<EMIN, EMAX><<<grid, kThreads, kSmemBytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int EMIN, int EMAX>
+cudaError_t prepare_range() {
+  return cudaFuncSetAttribute(knn_fused_kernel<EMIN, EMAX>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+template <int EMIN, int EMAX>
+cudaError_t occupancy_range(int* ctas) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_fused_kernel<EMIN, EMAX>,
+                                                       kThreads, kSmemBytes);
+}
+
+}  // namespace
+
+int knn_block_threads() { return kThreads; }
+int knn_queries_per_thread() { return kQ; }
+size_t knn_smem_bytes(int, int) { return kSmemBytes; }
+
+// Instantiations: one kernel per single E (used when a plan has one E) and
+// one for the whole range 1..10 (mixed sweeps).
+#define CCM_FOR_RANGES(X) \
+  X(1, 1) X(2, 2) X(3, 3) X(4, 4) X(5, 5) X(6, 6) X(7, 7) X(8, 8) X(9, 9) X(10, 10) X(1, 10)
+
+cudaError_t launch_knn(const KnnParams& p, int emin, int emax, int grid, cudaStream_t s) {
+#define CCM_LAUNCH(A, B) \
+  if (emin == A && emax == B) return launch_range<A, B>(p, grid, s);
+  CCM_FOR_RANGES(CCM_LAUNCH)
+#undef CCM_LAUNCH
+  if (emin >= 1 && emax <= kMaxE) return launch_range<1, 10>(p, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t knn_prepare() {
+#define CCM_PREP(A, B)                           \
+  {                                              \
+    const cudaError_t e = prepare_range<A, B>(); \
+    if (e != cudaSuccess) return e;              \
+  }
+  CCM_FOR_RANGES(CCM_PREP)
+#undef CCM_PREP
+  return cudaSuccess;
+}
+
+cudaError_t knn_occupancy(int emin, int emax, int* ctas) {
+#define CCM_OCC(A, B) \
+  if (emin == A && emax == B) return occupancy_range<A, B>(ctas);
+  CCM_FOR_RANGES(CCM_OCC)
+#undef CCM_OCC
+  if (emin >= 1 && emax <= kMaxE) return occupancy_range<1, 10>(ctas);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ccm

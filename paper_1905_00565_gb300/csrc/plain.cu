@@ -1,0 +1,140 @@
+// Plain GPU CCM: the straightforward CUDA form of one realization, kept as
+// the comparator the batched path is measured against.  Per realization it
+// launches the sampler for one unit, a naive kNN kernel (one thread per
+// query, library coordinates gathered from global memory for every query,
+// a sorted insertion into a local top-(E+2) list) that writes the
+// predictions, and a one-CTA FP64 Pearson kernel.  Same selection rule and
+// rounding sequence as the fused kernel, hence the same neighbours.
+#include <math.h>
+
+#include "ccm_internal.h"
+
+namespace ccm {
+namespace {
+
+constexpr int kPlainThreads = 128;
+constexpr int kRhoThreads = 1024;
+
+__global__ void __launch_bounds__(kPlainThreads)
+plain_knn_kernel(const float* series, const UnitDesc* unit, const int32_t* lib, float* xhat,
+                 int32_t* dbg_nbr, float* dbg_xhat) {
+  const UnitDesc u = *unit;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= u.n_m) return;
+  const int E = u.E, tau = u.tau, off = (E - 1) * tau, K = E + 2;
+  const float* sj = series + u.series_off + (int64_t)u.j * u.n;
+  const float* si = series + u.series_off + (int64_t)u.i * u.n;
+  const int32_t* ul = lib + u.lib_off;
+  float q[kMaxE];
+  for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
+  float kd[kMaxE + 2];
+  int kl[kMaxE + 2];
+  for (int s = 0; s < K; ++s) {
+    kd[s] = INFINITY;
+    kl[s] = -1;
+  }
+  for (int a = 0; a < u.L; ++a) {
+    const int l = ul[a];
+    float diff = __fsub_rn(q[0], sj[l + off]);
+    float acc = __fmul_rn(diff, diff);
+    for (int e = 1; e < E; ++e) {
+      diff = __fsub_rn(q[e], sj[l + off - e * tau]);
+      acc = __fmaf_rn(diff, diff, acc);
+    }
+    if (acc < kd[K - 1]) {
+      int s = K - 1;
+      while (s > 0 && acc < kd[s - 1]) {
+        kd[s] = kd[s - 1];
+        kl[s] = kl[s - 1];
+        --s;
+      }
+      kd[s] = acc;
+      kl[s] = l;
+    }
+  }
+  // drop the query itself, then simplex projection
+  int self = K;
+  for (int s = 0; s < K; ++s)
+    if (kl[s] == m) {
+      self = s;
+      break;
+    }
+  for (int s = self; s + 1 < K; ++s) {
+    kd[s] = kd[s + 1];
+    kl[s] = kl[s + 1];
+  }
+  const float d1 = sqrtf(kd[0]);
+  float usum = 0.f, accx = 0.f;
+  for (int s = 0; s <= E; ++s) {
+    const float di = sqrtf(kd[s]);
+    const float ui = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
+    usum += ui;
+    const int nbc = min(max(kl[s], 0), u.n_m - 1);  // in bounds even for non-finite input
+    accx = fmaf(ui, si[nbc + off], accx);
+  }
+  const float xh = accx / usum;
+  xhat[m] = xh;
+  if (dbg_xhat) dbg_xhat[u.q_off + m] = xh;
+  if (dbg_nbr)
+    for (int s = 0; s <= E; ++s) dbg_nbr[u.nbr_off + (int64_t)m * (E + 1) + s] = kl[s];
+}
+
+__global__ void __launch_bounds__(kRhoThreads)
+plain_rho_kernel(const float* series, const UnitDesc* unit, const float* xhat, double* rho) {
+  __shared__ double s_a[kRhoThreads], s_b[kRhoThreads], s_c[kRhoThreads];
+  const UnitDesc u = *unit;
+  const int off = (u.E - 1) * u.tau;
+  const float* si = series + u.series_off + (int64_t)u.i * u.n;
+  double a = 0.0, b = 0.0;
+  for (int m = threadIdx.x; m < u.n_m; m += blockDim.x) {
+    a += (double)si[m + off];
+    b += (double)xhat[m];
+  }
+  s_a[threadIdx.x] = a;
+  s_b[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s_a[threadIdx.x] += s_a[threadIdx.x + w];
+      s_b[threadIdx.x] += s_b[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  const double mx = s_a[0] / u.n_m, my = s_b[0] / u.n_m;
+  __syncthreads();
+  double xx = 0.0, yy = 0.0, xy = 0.0;
+  for (int m = threadIdx.x; m < u.n_m; m += blockDim.x) {
+    const double x = (double)si[m + off] - mx, y = (double)xhat[m] - my;
+    xx += x * x;
+    yy += y * y;
+    xy += x * y;
+  }
+  s_a[threadIdx.x] = xx;
+  s_b[threadIdx.x] = yy;
+  s_c[threadIdx.x] = xy;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s_a[threadIdx.x] += s_a[threadIdx.x + w];
+      s_b[threadIdx.x] += s_b[threadIdx.x + w];
+      s_c[threadIdx.x] += s_c[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    rho[u.out_idx] = (s_a[0] > 0.0 && s_b[0] > 0.0) ? s_c[0] / sqrt(s_a[0] * s_b[0]) : nan("");
+}
+
+}  // namespace
+
+cudaError_t launch_plain_unit(const float* series, const UnitDesc* unit_dev, const UnitDesc& unit,
+                              const int32_t* lib, float* xhat_scratch, double* rho_out,
+                              int32_t* dbg_nbr, float* dbg_xhat, int32_t*, cudaStream_t s) {
+  const unsigned grid = (unsigned)((unit.n_m + kPlainThreads - 1) / kPlainThreads);
+  plain_knn_kernel<<<grid, kPlainThreads, 0, s>>>(series, unit_dev, lib, xhat_scratch, dbg_nbr,
+                                                  dbg_xhat);
+  plain_rho_kernel<<<1, kRhoThreads, 0, s>>>(series, unit_dev, xhat_scratch, rho_out);
+  return cudaGetLastError();
+}
+
+}  // namespace ccm

@@ -1,0 +1,857 @@
+// Host runtime of the CCM library: the C ABI of include/ccm.h.
+//
+//  * context: device, device-memory budget, one-time kernel set-up, serving
+//    thread;
+//  * plan: validated copy of a problem, its realizations ("units") in output
+//    order, the work list of (unit, query tile) items sorted by decreasing
+//    cost, and one device arena for series, libraries, partial moments and rho;
+//  * run: sampler launch + one persistent fused-kernel launch, captured once
+//    into a CUDA graph and replayed;
+//  * plain comparator: one launch sequence per realization;
+//  * serving: queued jobs are admitted while their footprints fit the free
+//    budget, admitted jobs are batched into shared launches on a pool of
+//    streams, and results are copied back per job.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ccm.h"
+#include "ccm_internal.h"
+
+using namespace ccm;
+
+namespace {
+
+thread_local std::string t_err;
+
+ccm_status fail(ccm_status st, const std::string& msg) {
+  t_err = msg;
+  return st;
+}
+
+#define CCM_CUDA(call)                                                                   \
+  do {                                                                                   \
+    const cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(CCM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- problem ---
+struct ProblemCopy {
+  int32_t V = 0;
+  int64_t n = 0;
+  std::vector<int32_t> pairs, E, tau;
+  std::vector<int64_t> L;
+  int32_t r = 0;
+  uint64_t seed = 0;
+  uint32_t flags = 0;
+
+  int64_t n_units() const {
+    return (int64_t)(pairs.size() / 2) * (int64_t)E.size() * (int64_t)tau.size() *
+           (int64_t)L.size() * r;
+  }
+};
+
+ccm_status copy_problem(const ccm_problem* p, ProblemCopy* pc) {
+  if (!p) return fail(CCM_EINVAL, "problem is NULL");
+  if (p->n_series < 2) return fail(CCM_EINVAL, "n_series must be >= 2");
+  if (p->n < 3 || p->n > 0x7fffffff) return fail(CCM_EINVAL, "series length out of range");
+  if (p->n_pairs < 1 || !p->pairs) return fail(CCM_EINVAL, "no pairs");
+  if (p->n_E < 1 || !p->E || p->n_tau < 1 || !p->tau || p->n_L < 1 || !p->L)
+    return fail(CCM_EINVAL, "empty E, tau or L grid");
+  if (p->r < 1) return fail(CCM_EINVAL, "r must be >= 1");
+  pc->V = p->n_series;
+  pc->n = p->n;
+  pc->pairs.assign(p->pairs, p->pairs + 2 * (size_t)p->n_pairs);
+  pc->E.assign(p->E, p->E + p->n_E);
+  pc->tau.assign(p->tau, p->tau + p->n_tau);
+  pc->L.assign(p->L, p->L + p->n_L);
+  pc->r = p->r;
+  pc->seed = p->seed;
+  pc->flags = p->flags;
+  for (int32_t q = 0; q < p->n_pairs; ++q) {
+    const int32_t j = pc->pairs[2 * q], i = pc->pairs[2 * q + 1];
+    if (j < 0 || j >= pc->V || i < 0 || i >= pc->V || i == j)
+      return fail(CCM_EINVAL, "pair " + std::to_string(q) + " is invalid (need 0<=i,j<V, i!=j)");
+  }
+  for (int32_t E : pc->E)
+    if (E < 1 || E > kMaxE) return fail(CCM_EINVAL, "E must be in 1..10");
+  for (int32_t t : pc->tau)
+    if (t < 1) return fail(CCM_EINVAL, "tau must be >= 1");
+  for (int32_t E : pc->E)
+    for (int32_t t : pc->tau) {
+      const int64_t n_m = pc->n - (int64_t)(E - 1) * t;
+      for (int64_t L : pc->L)
+        if (L < E + 2 || L > n_m)
+          return fail(CCM_EINVAL, "L=" + std::to_string(L) + " outside [E+2, N_m] for E=" +
+                                      std::to_string(E) + ", tau=" + std::to_string(t));
+    }
+  if ((double)pc->n_units() > 2.0e9) return fail(CCM_EINVAL, "too many realizations");
+  return CCM_OK;
+}
+
+bool all_finite(const float* x, size_t count) {
+  for (size_t q = 0; q < count; ++q)
+    if (!std::isfinite(x[q])) return false;
+  return true;
+}
+
+// ------------------------------------------------------------- unit lists ---
+struct UnitList {
+  std::vector<UnitDesc> units;
+  std::vector<WorkItem> items;
+  std::vector<double> item_cost;
+  int64_t lib_total = 0, part_total = 0, q_total = 0, nbr_total = 0;
+  int emin = kMaxE + 1, emax = 0, max_nm = 0;
+  double pairs = 0.0, flops = 0.0;
+};
+
+// Append the units of one problem.  Offsets: series block, first rho index.
+void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, UnitList* ul) {
+  const int tileq = knn_block_threads() * knn_queries_per_thread();
+  const int64_t nP = (int64_t)pc.pairs.size() / 2;
+  int64_t out = out_base;
+  for (int64_t p = 0; p < nP; ++p)
+    for (int32_t E : pc.E)
+      for (int32_t tau : pc.tau)
+        for (int64_t L : pc.L)
+          for (int32_t k = 0; k < pc.r; ++k) {
+            UnitDesc u;
+            std::memset(&u, 0, sizeof(u));
+            u.series_off = series_off;
+            u.n = pc.n;
+            u.j = pc.pairs[2 * p];
+            u.i = pc.pairs[2 * p + 1];
+            u.E = E;
+            u.tau = tau;
+            u.L = (int32_t)L;
+            u.k = k;
+            u.seed = pc.seed;
+            u.n_m = (int32_t)(pc.n - (int64_t)(E - 1) * tau);
+            u.n_tiles = (u.n_m + tileq - 1) / tileq;
+            u.lib_off = ul->lib_total;
+            u.part_off = ul->part_total;
+            u.q_off = ul->q_total;
+            u.nbr_off = ul->nbr_total;
+            u.out_idx = out++;
+            const int32_t uidx = (int32_t)ul->units.size();
+            for (int32_t t = 0; t < u.n_tiles; ++t) {
+              const int64_t nq = std::min<int64_t>(tileq, u.n_m - (int64_t)t * tileq);
+              ul->items.push_back(WorkItem{uidx, t});
+              // distance work plus a fixed cost per library point for staging
+              ul->item_cost.push_back((double)L * ((double)nq * (2.0 * E + 1.0) + 64.0 * E));
+            }
+            ul->lib_total += L;
+            ul->part_total += u.n_tiles;
+            ul->q_total += u.n_m;
+            ul->nbr_total += (int64_t)u.n_m * (E + 1);
+            ul->emin = std::min(ul->emin, E);
+            ul->emax = std::max(ul->emax, E);
+            ul->max_nm = std::max(ul->max_nm, u.n_m);
+            ul->pairs += (double)u.n_m * (double)L;
+            ul->flops += 3.0 * E * (double)u.n_m * (double)L;
+            ul->units.push_back(u);
+          }
+}
+
+// Sort the work list by decreasing cost (longest first), ties by position.
+void sort_items(UnitList* ul) {
+  std::vector<int64_t> order(ul->items.size());
+  for (size_t q = 0; q < order.size(); ++q) order[q] = (int64_t)q;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return ul->item_cost[(size_t)a] > ul->item_cost[(size_t)b];
+  });
+  std::vector<WorkItem> sorted(order.size());
+  for (size_t q = 0; q < order.size(); ++q) sorted[q] = ul->items[(size_t)order[q]];
+  ul->items.swap(sorted);
+}
+
+// Device arena layout for a unit list.
+struct Arena {
+  size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
+         counter = 0, scratch = 0, total = 0;
+};
+
+Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
+  Arena a;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  a.series = take(sizeof(float) * (size_t)series_elems);
+  a.units = take(sizeof(UnitDesc) * ul.units.size());
+  a.items = take(sizeof(WorkItem) * ul.items.size());
+  a.lib = take(sizeof(int32_t) * (size_t)ul.lib_total);
+  a.part = take(6 * sizeof(double) * (size_t)ul.part_total);
+  a.done = take(sizeof(uint32_t) * ul.units.size());
+  a.rho = take(sizeof(double) * (size_t)n_rho);
+  a.err = take(sizeof(int32_t));
+  a.counter = take(sizeof(uint32_t));
+  a.scratch = take(sizeof(float) * (size_t)scratch_floats);
+  a.total = o;
+  return a;
+}
+
+}  // namespace
+
+// ================================================================ context ===
+struct Job;
+struct Batch;
+
+struct ccm_context {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  int sm_count = 0;
+  std::mutex mu;  // budget, job table, queue, batches
+  std::condition_variable cv;
+  // serving state
+  std::thread server;
+  bool server_started = false;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::map<uint64_t, std::shared_ptr<Job>> jobs;
+  std::deque<std::shared_ptr<Job>> queue;
+  std::list<std::shared_ptr<Batch>> inflight;
+  std::vector<cudaStream_t> streams;
+  size_t next_stream = 0;
+  int max_inflight = 4;
+};
+
+namespace {
+
+ccm_status reserve(ccm_context* ctx, size_t bytes) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (bytes > ctx->budget)
+    return fail(CCM_ETOOLARGE, "footprint " + std::to_string(bytes) + " B exceeds budget " +
+                                   std::to_string(ctx->budget) + " B");
+  if (ctx->used + bytes > ctx->budget)
+    return fail(CCM_ENOMEM, "budget in use: " + std::to_string(ctx->used) + " of " +
+                                std::to_string(ctx->budget) + " B");
+  ctx->used += bytes;
+  return CCM_OK;
+}
+
+void release(ccm_context* ctx, size_t bytes) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->used -= std::min(ctx->used, bytes);
+}
+
+}  // namespace
+
+// =================================================================== plan ===
+struct ccm_plan_s {
+  ccm_context* ctx = nullptr;
+  ProblemCopy pc;
+  UnitList ul;
+  Arena ar;
+  char* d_arena = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int grid = 0;
+  std::mutex run_mu;
+  ccm_plan_info info{};
+};
+
+namespace {
+
+SamplerParams sampler_params(char* base, const Arena& ar) {
+  SamplerParams sp{};
+  sp.units = reinterpret_cast<const UnitDesc*>(base + ar.units);
+  sp.lib = reinterpret_cast<int32_t*>(base + ar.lib);
+  sp.err = reinterpret_cast<int32_t*>(base + ar.err);
+  return sp;
+}
+
+KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persistent) {
+  KnnParams kp{};
+  kp.series = reinterpret_cast<const float*>(base + ar.series);
+  kp.units = reinterpret_cast<const UnitDesc*>(base + ar.units);
+  kp.items = reinterpret_cast<const WorkItem*>(base + ar.items);
+  kp.n_items = (int64_t)ul.items.size();
+  kp.lib = reinterpret_cast<const int32_t*>(base + ar.lib);
+  kp.partials = reinterpret_cast<double*>(base + ar.part);
+  kp.unit_done = reinterpret_cast<uint32_t*>(base + ar.done);
+  kp.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter);
+  kp.rho = reinterpret_cast<double*>(base + ar.rho);
+  kp.err = reinterpret_cast<int32_t*>(base + ar.err);
+  kp.persistent = persistent;
+  return kp;
+}
+
+// Enqueue sampler + fused kernel for a whole unit list on stream s.
+ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int grid, int persistent,
+                         int32_t* dbg_lib, const int64_t* d_dbg_lib_off, int32_t* dbg_nbr,
+                         float* dbg_xhat, cudaStream_t s) {
+  CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
+  CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, sizeof(uint32_t), s));
+  CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
+  SamplerParams sp = sampler_params(base, ar);
+  sp.dbg_lib = dbg_lib;
+  sp.dbg_lib_off = d_dbg_lib_off;
+  CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
+  KnnParams kp = knn_params(base, ar, ul, persistent);
+  kp.dbg_nbr = dbg_nbr;
+  kp.dbg_xhat = dbg_xhat;
+  const int g = persistent ? grid : (int)ul.items.size();
+  CCM_CUDA(launch_knn(kp, ul.emin, ul.emax, g, s));
+  return CCM_OK;
+}
+
+ccm_status check_err_flag(char* base, const Arena& ar, cudaStream_t s) {
+  int32_t err = 0;
+  CCM_CUDA(cudaMemcpyAsync(&err, base + ar.err, sizeof(err), cudaMemcpyDeviceToHost, s));
+  CCM_CUDA(cudaStreamSynchronize(s));
+  if (err != 0) return fail(CCM_ECUDA, "kernel reported error flag " + std::to_string(err));
+  return CCM_OK;
+}
+
+int persistent_grid(ccm_context* ctx, int emin, int emax) {
+  int per_sm = 1;
+  if (knn_occupancy(emin, emax, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return ctx->sm_count * per_sm;
+}
+
+}  // namespace
+
+// ==================================================================== ABI ===
+extern "C" {
+
+const char* ccm_last_error(void) { return t_err.c_str(); }
+
+const char* ccm_version(void) { return "ccm-gb300 0.1 (sm_103a)"; }
+
+ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context** out) {
+  if (!out) return fail(CCM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  CCM_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fail(CCM_EINVAL, "no such device");
+  CCM_CUDA(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  CCM_CUDA(cudaGetDeviceProperties(&prop, device));
+  if (prop.major < 10) return fail(CCM_EINVAL, "needs a Blackwell (sm_10x) GPU");
+  CCM_CUDA(sampler_prepare());
+  CCM_CUDA(knn_prepare());
+  size_t free_b = 0, total_b = 0;
+  CCM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  std::unique_ptr<ccm_context> ctx(new ccm_context());
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+  *out = ctx.release();
+  return CCM_OK;
+}
+
+ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out) {
+  if (!ctx || !out) return fail(CCM_EINVAL, "NULL argument");
+  *out = nullptr;
+  std::unique_ptr<ccm_plan_s> pl(new ccm_plan_s());
+  pl->ctx = ctx;
+  ccm_status st = copy_problem(prob, &pl->pc);
+  if (st != CCM_OK) return st;
+  append_units(pl->pc, 0, 0, &pl->ul);
+  sort_items(&pl->ul);
+  const int64_t series_elems = (int64_t)pl->pc.V * pl->pc.n;
+  pl->ar = layout(series_elems, pl->ul, (int64_t)pl->ul.units.size(), pl->ul.max_nm);
+  CCM_CUDA(cudaSetDevice(ctx->device));
+  st = reserve(ctx, pl->ar.total);
+  if (st != CCM_OK) return st;
+  cudaError_t e = cudaMalloc(&pl->d_arena, pl->ar.total);
+  if (e != cudaSuccess) {
+    release(ctx, pl->ar.total);
+    return fail(CCM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  e = cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_arena + pl->ar.units, pl->ul.units.data(),
+                   sizeof(UnitDesc) * pl->ul.units.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_arena + pl->ar.items, pl->ul.items.data(),
+                   sizeof(WorkItem) * pl->ul.items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemset(pl->d_arena + pl->ar.done, 0, sizeof(uint32_t) * pl->ul.units.size());
+  if (e != cudaSuccess) {
+    cudaFree(pl->d_arena);
+    if (pl->stream) cudaStreamDestroy(pl->stream);
+    release(ctx, pl->ar.total);
+    return fail(CCM_ECUDA, std::string("plan set-up: ") + cudaGetErrorString(e));
+  }
+  pl->grid = persistent_grid(ctx, pl->ul.emin, pl->ul.emax);
+  ccm_plan_info& in = pl->info;
+  in.n_units = (int64_t)pl->ul.units.size();
+  in.n_queries = pl->ul.q_total;
+  in.library_entries = pl->ul.lib_total;
+  in.neighbour_entries = pl->ul.nbr_total;
+  in.n_work_items = (int64_t)pl->ul.items.size();
+  in.device_bytes = pl->ar.total;
+  in.pair_count = pl->ul.pairs;
+  in.flop_count = pl->ul.flops;
+  *out = pl.release();
+  return CCM_OK;
+}
+
+ccm_status ccm_plan_get_info(const ccm_plan_t* plan, ccm_plan_info* info) {
+  if (!plan || !info) return fail(CCM_EINVAL, "NULL argument");
+  *info = plan->info;
+  return CCM_OK;
+}
+
+ccm_status ccm_plan_destroy(ccm_plan_t* plan) {
+  if (!plan) return fail(CCM_EINVAL, "plan is NULL");
+  cudaSetDevice(plan->ctx->device);
+  if (plan->stream) cudaStreamSynchronize(plan->stream);
+  if (plan->graph) cudaGraphExecDestroy(plan->graph);
+  if (plan->stream) cudaStreamDestroy(plan->stream);
+  cudaFree(plan->d_arena);
+  release(plan->ctx, plan->ar.total);
+  delete plan;
+  return CCM_OK;
+}
+
+ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const ccm_debug_out* dbg,
+                      void* cuda_stream) {
+  if (!plan || !series || !rho) return fail(CCM_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(plan->run_mu);
+  CCM_CUDA(cudaSetDevice(plan->ctx->device));
+  const ProblemCopy& pc = plan->pc;
+  const bool in_dev = (pc.flags & CCM_INPUT_ON_DEVICE) != 0;
+  const bool out_dev = (pc.flags & CCM_OUTPUT_ON_DEVICE) != 0;
+  const size_t series_bytes = sizeof(float) * (size_t)pc.V * (size_t)pc.n;
+  if (!in_dev && !all_finite(series, (size_t)pc.V * (size_t)pc.n))
+    return fail(CCM_EINVAL, "series holds a non-finite value");
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : plan->stream;
+  char* base = plan->d_arena;
+  CCM_CUDA(cudaMemcpyAsync(base + plan->ar.series, series, series_bytes,
+                           in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  const bool want_dbg = dbg && (dbg->libraries || dbg->neighbours || dbg->predictions);
+  if (want_dbg) {
+    // Checking path: direct launches with the per-unit outputs (no graph).
+    const UnitList& ul = plan->ul;
+    std::vector<int64_t> lib_off(ul.units.size());
+    for (size_t q = 0; q < ul.units.size(); ++q) lib_off[q] = ul.units[q].lib_off;
+    const size_t lb = sizeof(int32_t) * (size_t)ul.lib_total;
+    const size_t nb = sizeof(int32_t) * (size_t)ul.nbr_total;
+    const size_t xb = sizeof(float) * (size_t)ul.q_total;
+    const size_t ob = sizeof(int64_t) * lib_off.size();
+    char* tmp = nullptr;
+    const size_t tmp_bytes = align_up(ob, 256) + (out_dev ? 0 : align_up(lb, 256) +
+                                                  align_up(nb, 256) + align_up(xb, 256));
+    CCM_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
+    int64_t* d_off = reinterpret_cast<int64_t*>(tmp);
+    char* t2 = tmp + align_up(ob, 256);
+    int32_t* d_lib = dbg->libraries ? (out_dev ? dbg->libraries : reinterpret_cast<int32_t*>(t2))
+                                    : nullptr;
+    int32_t* d_nbr = dbg->neighbours ? (out_dev ? dbg->neighbours
+                                                : reinterpret_cast<int32_t*>(t2 + align_up(lb, 256)))
+                                     : nullptr;
+    float* d_xh = dbg->predictions
+                      ? (out_dev ? dbg->predictions
+                                 : reinterpret_cast<float*>(t2 + align_up(lb, 256) + align_up(nb, 256)))
+                      : nullptr;
+    CCM_CUDA(cudaMemcpyAsync(d_off, lib_off.data(), ob, cudaMemcpyHostToDevice, s));
+    ccm_status st = enqueue_sweep(base, plan->ar, ul, plan->grid, 1, d_lib, d_off, d_nbr, d_xh, s);
+    if (st != CCM_OK) return st;
+    if (!out_dev) {
+      if (dbg->libraries) CCM_CUDA(cudaMemcpyAsync(dbg->libraries, d_lib, lb, cudaMemcpyDeviceToHost, s));
+      if (dbg->neighbours) CCM_CUDA(cudaMemcpyAsync(dbg->neighbours, d_nbr, nb, cudaMemcpyDeviceToHost, s));
+      if (dbg->predictions) CCM_CUDA(cudaMemcpyAsync(dbg->predictions, d_xh, xb, cudaMemcpyDeviceToHost, s));
+    }
+    CCM_CUDA(cudaFreeAsync(tmp, s));
+  } else {
+    if (!plan->graph) {
+      cudaGraph_t graph = nullptr;
+      CCM_CUDA(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
+      ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->grid, 1, nullptr, nullptr,
+                                    nullptr, nullptr, plan->stream);
+      const cudaError_t ce = cudaStreamEndCapture(plan->stream, &graph);
+      if (st != CCM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      CCM_CUDA(ce);
+      const cudaError_t ie = cudaGraphInstantiate(&plan->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      CCM_CUDA(ie);
+    }
+    CCM_CUDA(cudaGraphLaunch(plan->graph, s));
+  }
+  const size_t rho_bytes = sizeof(double) * plan->ul.units.size();
+  CCM_CUDA(cudaMemcpyAsync(rho, base + plan->ar.rho, rho_bytes,
+                           out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!cuda_stream || !in_dev || !out_dev) return check_err_flag(base, plan->ar, s);
+  return CCM_OK;
+}
+
+ccm_status ccm_run(ccm_plan_t* plan, const float* series, double* rho, void* cuda_stream) {
+  return ccm_run_ex(plan, series, rho, nullptr, cuda_stream);
+}
+
+ccm_status ccm_run_plain(ccm_plan_t* plan, const float* series, double* rho, void* cuda_stream) {
+  if (!plan || !series || !rho) return fail(CCM_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(plan->run_mu);
+  CCM_CUDA(cudaSetDevice(plan->ctx->device));
+  const ProblemCopy& pc = plan->pc;
+  const bool in_dev = (pc.flags & CCM_INPUT_ON_DEVICE) != 0;
+  const bool out_dev = (pc.flags & CCM_OUTPUT_ON_DEVICE) != 0;
+  if (!in_dev && !all_finite(series, (size_t)pc.V * (size_t)pc.n))
+    return fail(CCM_EINVAL, "series holds a non-finite value");
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : plan->stream;
+  char* base = plan->d_arena;
+  const Arena& ar = plan->ar;
+  CCM_CUDA(cudaMemcpyAsync(base + ar.series, series, sizeof(float) * (size_t)pc.V * (size_t)pc.n,
+                           in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
+  const SamplerParams sp = sampler_params(base, ar);
+  const UnitDesc* d_units = reinterpret_cast<const UnitDesc*>(base + ar.units);
+  for (size_t q = 0; q < plan->ul.units.size(); ++q) {
+    const UnitDesc& u = plan->ul.units[q];
+    CCM_CUDA(launch_sampler(sp, (int64_t)q, 1, u.n_m, s));
+    CCM_CUDA(launch_plain_unit(reinterpret_cast<const float*>(base + ar.series), d_units + q, u,
+                               reinterpret_cast<const int32_t*>(base + ar.lib),
+                               reinterpret_cast<float*>(base + ar.scratch),
+                               reinterpret_cast<double*>(base + ar.rho), nullptr, nullptr,
+                               reinterpret_cast<int32_t*>(base + ar.err), s));
+  }
+  CCM_CUDA(cudaMemcpyAsync(rho, base + ar.rho, sizeof(double) * plan->ul.units.size(),
+                           out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!cuda_stream || !in_dev || !out_dev) return check_err_flag(base, ar, s);
+  return CCM_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ serving ===
+struct Job {
+  uint64_t ticket = 0;
+  ProblemCopy pc;
+  float* h_series = nullptr;  // pinned copy
+  double* h_rho = nullptr;    // pinned result
+  int64_t n_units = 0;
+  size_t footprint = 0;
+  enum State { kQueued, kRunning, kDone, kFailed, kCancelled } state = kQueued;
+  ccm_status status = CCM_PENDING;
+  std::string err;
+  double t_submit = 0, t_start = 0, t_finish = 0;
+};
+
+struct Batch {
+  ccm_context* ctx = nullptr;
+  std::vector<std::shared_ptr<Job>> jobs;
+  UnitList ul;
+  Arena ar;
+  char* d_arena = nullptr;
+  int32_t* h_err = nullptr;
+  cudaStream_t stream = nullptr;
+  std::atomic<bool> finished{false};
+};
+
+namespace {
+
+size_t job_footprint(const ProblemCopy& pc) {
+  UnitList ul;
+  append_units(pc, 0, 0, &ul);
+  return layout((int64_t)pc.V * pc.n, ul, (int64_t)ul.units.size(), 0).total;
+}
+
+void CUDART_CB on_batch_done(void* arg) {
+  Batch* b = static_cast<Batch*>(arg);
+  ccm_context* ctx = b->ctx;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    b->finished.store(true);
+  }
+  ctx->cv.notify_all();
+}
+
+// Launch one batch (called by the serving thread without ctx->mu held).
+ccm_status launch_batch(ccm_context* ctx, Batch* b) {
+  int64_t series_elems = 0, out = 0;
+  for (auto& j : b->jobs) {
+    append_units(j->pc, series_elems, out, &b->ul);
+    series_elems += (int64_t)j->pc.V * j->pc.n;
+    out += j->n_units;
+  }
+  sort_items(&b->ul);
+  b->ar = layout(series_elems, b->ul, out, 0);
+  CCM_CUDA(cudaMallocAsync(&b->d_arena, b->ar.total, b->stream));
+  char* base = b->d_arena;
+  int64_t so = 0;
+  for (auto& j : b->jobs) {
+    const size_t bytes = sizeof(float) * (size_t)j->pc.V * (size_t)j->pc.n;
+    CCM_CUDA(cudaMemcpyAsync(base + b->ar.series + sizeof(float) * so, j->h_series, bytes,
+                             cudaMemcpyHostToDevice, b->stream));
+    so += (int64_t)j->pc.V * j->pc.n;
+  }
+  CCM_CUDA(cudaMemcpyAsync(base + b->ar.units, b->ul.units.data(),
+                           sizeof(UnitDesc) * b->ul.units.size(), cudaMemcpyHostToDevice, b->stream));
+  CCM_CUDA(cudaMemcpyAsync(base + b->ar.items, b->ul.items.data(),
+                           sizeof(WorkItem) * b->ul.items.size(), cudaMemcpyHostToDevice, b->stream));
+  CCM_CUDA(cudaMemsetAsync(base + b->ar.done, 0, sizeof(uint32_t) * b->ul.units.size(), b->stream));
+  ccm_status st = enqueue_sweep(base, b->ar, b->ul, 0, 0, nullptr, nullptr, nullptr, nullptr,
+                                b->stream);
+  if (st != CCM_OK) return st;
+  int64_t ro = 0;
+  for (auto& j : b->jobs) {
+    CCM_CUDA(cudaMemcpyAsync(j->h_rho, base + b->ar.rho + sizeof(double) * ro,
+                             sizeof(double) * (size_t)j->n_units, cudaMemcpyDeviceToHost, b->stream));
+    ro += j->n_units;
+  }
+  CCM_CUDA(cudaMemcpyAsync(b->h_err, base + b->ar.err, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           b->stream));
+  CCM_CUDA(cudaFreeAsync(b->d_arena, b->stream));
+  CCM_CUDA(cudaLaunchHostFunc(b->stream, on_batch_done, b));
+  return CCM_OK;
+}
+
+void serve(ccm_context* ctx) {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  for (;;) {
+    // Retire finished batches.
+    for (auto it = ctx->inflight.begin(); it != ctx->inflight.end();) {
+      Batch* b = it->get();
+      if (!b->finished.load()) {
+        ++it;
+        continue;
+      }
+      const double t = now_s();
+      size_t bytes = 0;
+      for (auto& j : b->jobs) {
+        bytes += j->footprint;
+        j->t_finish = t;
+        if (*b->h_err != 0) {
+          j->state = Job::kFailed;
+          j->status = CCM_ECUDA;
+          j->err = "kernel reported error flag " + std::to_string(*b->h_err);
+        } else {
+          j->state = Job::kDone;
+          j->status = CCM_OK;
+        }
+      }
+      ctx->used -= std::min(ctx->used, bytes);
+      cudaFreeHost(b->h_err);
+      it = ctx->inflight.erase(it);
+      ctx->cv.notify_all();
+    }
+    if (ctx->stop && ctx->inflight.empty()) break;
+    // Admit queued jobs into a new batch while their footprints fit.
+    if (!ctx->stop && !ctx->queue.empty() && (int)ctx->inflight.size() < ctx->max_inflight) {
+      auto b = std::make_shared<Batch>();
+      b->ctx = ctx;
+      size_t bytes = 0;
+      int64_t units = 0;
+      while (!ctx->queue.empty()) {
+        auto& j = ctx->queue.front();
+        if (j->state == Job::kCancelled) {
+          ctx->queue.pop_front();
+          continue;
+        }
+        if (ctx->used + bytes + j->footprint > ctx->budget) break;
+        if (!b->jobs.empty() && units + j->n_units > (int64_t)1 << 22) break;
+        bytes += j->footprint;
+        units += j->n_units;
+        b->jobs.push_back(j);
+        ctx->queue.pop_front();
+      }
+      if (!b->jobs.empty()) {
+        ctx->used += bytes;
+        const double t = now_s();
+        for (auto& j : b->jobs) {
+          j->state = Job::kRunning;
+          j->t_start = t;
+        }
+        b->stream = ctx->streams[ctx->next_stream++ % ctx->streams.size()];
+        ctx->inflight.push_back(b);
+        lk.unlock();
+        cudaError_t he = cudaMallocHost(&b->h_err, sizeof(int32_t));
+        ccm_status st = (he == cudaSuccess) ? launch_batch(ctx, b.get())
+                                            : fail(CCM_ENOMEM, "pinned allocation failed");
+        lk.lock();
+        if (st != CCM_OK) {
+          // Nothing more will run for this batch once the stream drains.
+          lk.unlock();
+          cudaStreamSynchronize(b->stream);
+          if (b->d_arena) cudaFree(b->d_arena);
+          lk.lock();
+          for (auto& j : b->jobs) {
+            j->state = Job::kFailed;
+            j->status = st;
+            j->err = t_err;
+            j->t_finish = now_s();
+          }
+          ctx->used -= std::min(ctx->used, bytes);
+          if (b->h_err) cudaFreeHost(b->h_err);
+          ctx->inflight.remove(b);
+          ctx->cv.notify_all();
+        }
+        continue;
+      }
+    }
+    ctx->cv.wait_for(lk, std::chrono::milliseconds(50));
+  }
+}
+
+ccm_status ensure_server(ccm_context* ctx) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (ctx->server_started) return CCM_OK;
+  int lo = 0, hi = 0;
+  CCM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  for (int q = 0; q < ctx->max_inflight; ++q) {
+    cudaStream_t s;
+    CCM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ctx->streams.push_back(s);
+  }
+  ctx->server = std::thread(serve, ctx);
+  ctx->server_started = true;
+  return CCM_OK;
+}
+
+void free_job(Job* j) {
+  if (j->h_series) cudaFreeHost(j->h_series);
+  if (j->h_rho) cudaFreeHost(j->h_rho);
+  j->h_series = nullptr;
+  j->h_rho = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+ccm_status ccm_submit(ccm_context* ctx, const ccm_problem* prob, const float* series,
+                      uint64_t* ticket) {
+  if (!ctx || !series || !ticket) return fail(CCM_EINVAL, "NULL argument");
+  auto j = std::make_shared<Job>();
+  ccm_status st = copy_problem(prob, &j->pc);
+  if (st != CCM_OK) return st;
+  if (j->pc.flags & (CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE))
+    return fail(CCM_EINVAL, "ccm_submit takes host series and returns host rho");
+  const size_t elems = (size_t)j->pc.V * (size_t)j->pc.n;
+  if (!all_finite(series, elems)) return fail(CCM_EINVAL, "series holds a non-finite value");
+  j->n_units = j->pc.n_units();
+  j->footprint = job_footprint(j->pc);
+  if (j->footprint > ctx->budget)
+    return fail(CCM_ETOOLARGE, "job footprint " + std::to_string(j->footprint) +
+                                   " B exceeds the context budget");
+  CCM_CUDA(cudaSetDevice(ctx->device));
+  st = ensure_server(ctx);
+  if (st != CCM_OK) return st;
+  CCM_CUDA(cudaMallocHost(&j->h_series, sizeof(float) * elems));
+  cudaError_t e = cudaMallocHost(&j->h_rho, sizeof(double) * (size_t)j->n_units);
+  if (e != cudaSuccess) {
+    free_job(j.get());
+    return fail(CCM_ENOMEM, "pinned allocation failed");
+  }
+  std::memcpy(j->h_series, series, sizeof(float) * elems);
+  j->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    j->ticket = ctx->next_ticket++;
+    ctx->jobs[j->ticket] = j;
+    ctx->queue.push_back(j);
+  }
+  ctx->cv.notify_all();
+  *ticket = j->ticket;
+  return CCM_OK;
+}
+
+ccm_status ccm_poll(ccm_context* ctx, uint64_t ticket, double* rho, int32_t timeout_ms) {
+  if (!ctx) return fail(CCM_EINVAL, "context is NULL");
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  auto it = ctx->jobs.find(ticket);
+  if (it == ctx->jobs.end()) return fail(CCM_ENOTFOUND, "unknown ticket");
+  std::shared_ptr<Job> j = it->second;
+  auto finished = [&] {
+    return j->state == Job::kDone || j->state == Job::kFailed || j->state == Job::kCancelled;
+  };
+  if (!finished() && timeout_ms > 0)
+    ctx->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished);
+  if (!finished()) return CCM_PENDING;
+  ccm_status st = j->status;
+  if (j->state == Job::kDone) {
+    if (!rho) return fail(CCM_EINVAL, "rho is NULL");
+    std::memcpy(rho, j->h_rho, sizeof(double) * (size_t)j->n_units);
+  } else {
+    t_err = j->err;
+  }
+  ctx->jobs.erase(it);
+  lk.unlock();
+  free_job(j.get());
+  return st;
+}
+
+ccm_status ccm_cancel(ccm_context* ctx, uint64_t ticket) {
+  if (!ctx) return fail(CCM_EINVAL, "context is NULL");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->jobs.find(ticket);
+  if (it == ctx->jobs.end()) return fail(CCM_ENOTFOUND, "unknown ticket");
+  Job* j = it->second.get();
+  if (j->state != Job::kQueued) return CCM_PENDING;
+  j->state = Job::kCancelled;
+  j->status = CCM_ECANCELLED;
+  j->err = "cancelled";
+  j->t_finish = now_s();
+  ctx->cv.notify_all();
+  return CCM_OK;
+}
+
+ccm_status ccm_job_times(ccm_context* ctx, uint64_t ticket, double* submit_s, double* start_s,
+                         double* finish_s) {
+  if (!ctx) return fail(CCM_EINVAL, "context is NULL");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->jobs.find(ticket);
+  if (it == ctx->jobs.end()) return fail(CCM_ENOTFOUND, "unknown ticket");
+  Job* j = it->second.get();
+  if (submit_s) *submit_s = j->t_submit;
+  if (start_s) *start_s = j->t_start;
+  if (finish_s) *finish_s = j->t_finish;
+  return (j->state == Job::kDone || j->state == Job::kFailed || j->state == Job::kCancelled)
+             ? CCM_OK
+             : CCM_PENDING;
+}
+
+ccm_status ccm_context_destroy(ccm_context* ctx) {
+  if (!ctx) return fail(CCM_EINVAL, "context is NULL");
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->stop = true;
+    for (auto& j : ctx->queue) {
+      if (j->state == Job::kQueued) {
+        j->state = Job::kCancelled;
+        j->status = CCM_ECANCELLED;
+      }
+    }
+    ctx->queue.clear();
+  }
+  ctx->cv.notify_all();
+  if (ctx->server_started) ctx->server.join();
+  cudaSetDevice(ctx->device);
+  for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
+  for (auto& kv : ctx->jobs) free_job(kv.second.get());
+  ctx->jobs.clear();
+  delete ctx;
+  return CCM_OK;
+}
+
+}  // extern "C"

@@ -388,3 +388,14 @@ def test_convergence_of_the_coupled_logistic_map():
     assert strong[-1] > 0.8
     assert np.all(strong[2:] > weak[2:])
     assert np.all(np.isfinite(rho))
+
+
+def test_query_subset_matches_full_run():
+    s = I.logistic_pair(500)
+    lib = oracle.library(497, 200, 1, 4, 1, 2, 3)
+    nbr = oracle.neighbours(s[1], 4, 1, lib)
+    xh = oracle.predict(s[1], s[0], 4, 1, nbr)
+    q = np.array([0, 7, 250, 496])
+    nb2, xh2 = oracle.query_subset(s[1], s[0], 4, 1, lib, q)
+    assert np.array_equal(nb2, nbr[q])
+    assert np.array_equal(xh2, xh[q])
