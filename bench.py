@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the CCM hot path on GB300.
+
+Workload (one "step"): the batched parameter sweep over a coupled logistic map
+of N=10^4 FP32 points: E=1..10, tau=1..4, 20 library sizes log-spaced 100..9000,
+r=250 realizations, both directions (800 cells x 250 x 2 = 4*10^5
+realizations, 4.0*10^9 neighbour queries, 8.45*10^12 query-library pairs).
+One step = one ccm_run of the whole sweep (library sampler + one persistent
+fused kNN/simplex/rho launch, replayed from a CUDA graph).
+
+Prints one JSON line.  `value` is realizations/s with inputs resident on the
+device; `e2e` is the same metric through ccm_run with pinned host buffers
+(host->device series copy and device->host rho copy inside the timed region);
+`roofline` reports the fused kernel against the FP32 ALU peak; `cpu_baseline`
+is the CPU oracle on a bounded sample of the same workload; `vs_plain_gpu`
+compares with the one-launch-per-realization plain GPU CCM on a subset.
+
+Multi-GPU (torchrun): every rank runs its own replica of the sweep (no data
+exchange); the barrier and a max-reduction of the timings are the only
+collectives.  ``--impl reference`` times the CPU oracle instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CCM realizations/s & neighbour queries/s vs plain GPU CCM; p50/p99 job latency"
+UNIT = "realizations/s"
+# FP32 peak from unit counts and the maximum clock: 152 SMs x 128 FP32 lanes x
+# 2 flops per fused multiply-add x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+KNN_SRC = os.path.join(ROOT, "paper_1905_00565_gb300", "csrc", "knn_fused.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_fused_sweep_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample-units", type=int, default=96)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="R",
+                    help="only run every sweep cell with R realizations through ccm_run "
+                         "twice (the small case for ncu captures) and exit")
+    return ap.parse_args()
+
+
+def workload_config():
+    return {
+        "workload": "ccm-sweep: coupled logistic map N=10000 (rx=3.8, ry=3.5, bxy=0.02, "
+                    "byx=0.1), both directions, E=1..10, tau=1..4, 20 L log-spaced 100..9000, "
+                    "r=250",
+        "realizations": 400000,
+        "queries": 3995500000,
+        "pairs": 8451681150000,
+        "precision": "FP32 distances/selection/weights, FP64 rho moments",
+    }
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle ---
+def _oracle_unit(args):
+    import numpy as np  # noqa: F401
+    import oracle
+    series, j, i, E, tau, L, k, seed = args
+    return oracle.ccm_unit(series, j, i, E, tau, L, k, seed)
+
+
+def cpu_sample(p, n_units: int, seed: int = 1):
+    """A seeded uniform sample of realizations of the workload."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    total = p.n_units()
+    idx = rng.choice(total, size=min(n_units, total), replace=False)
+    shape = (len(p.pairs), len(p.E), len(p.tau), len(p.L), p.r)
+    tasks, pairs = [], 0.0
+    for flat in idx:
+        pi, e, t, l, k = np.unravel_index(int(flat), shape)
+        j, i = (int(x) for x in p.pairs[pi])
+        E, tau, L = int(p.E[e]), int(p.tau[t]), int(p.L[l])
+        tasks.append((p.series, j, i, E, tau, L, int(k), p.seed))
+        pairs += (p.n - (E - 1) * tau) * L
+    return tasks, pairs
+
+
+def time_cpu_oracle(p, n_units: int):
+    """Oracle over a bounded sample on all host cores (spawned workers)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    tasks, pairs = cpu_sample(p, n_units)
+    cores = os.cpu_count() or 1
+    ctxm = mp.get_context("spawn")
+    with ctxm.Pool(cores) as pool:
+        pool.map(_oracle_unit, tasks[:cores])          # warm the workers
+        t0 = time.perf_counter()
+        pool.map(_oracle_unit, tasks, chunksize=1)
+        dt = time.perf_counter() - t0
+    pairs_per_s = pairs / dt
+    value = pairs_per_s * p.n_units() / p.pair_count()
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(tasks)} realizations drawn uniformly (seed 1) from the sweep, "
+                      f"{pairs:.3e} query-library pairs in {dt:.1f} s wall on {cores} "
+                      f"processes; scaled to the sweep by pair count",
+            "pairs_per_s": pairs_per_s}
+
+
+# ------------------------------------------------------------ GPU arm ------
+def traffic_entry():
+    """DRAM bytes per fused-kernel launch from the committed ncu summary, if the
+    kernel source still matches the one that was profiled."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256(open(KNN_SRC, "rb").read()).hexdigest()
+    if rec.get("knn_fused_sha256") != h:
+        return None
+    return rec.get("dram_bytes_per_full_sweep_launch")
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1905_00565_gb300 import ccm
+    from paper_1905_00565_gb300 import inputs as I
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    p = I.sweep_problem()
+    ctx = ccm.ccm_context_create(local_rank)
+    dev_flags = ccm.CCM_INPUT_ON_DEVICE | ccm.CCM_OUTPUT_ON_DEVICE
+    plan = ccm.plan_problem(ctx, p, dev_flags)
+    info = ccm.ccm_plan_get_info(plan)
+    s_dev = torch.from_numpy(p.series).cuda()
+    rho_dev = torch.zeros(ccm.rho_shape(p), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+
+    for _ in range(args.warmup):
+        ccm.ccm_run(plan, s_dev, rho_dev, stream=stream)
+        stream.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, knn_ms, samp_ms = [], [], []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ccm.ccm_run(plan, s_dev, rho_dev, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        a, b = ccm.ccm_plan_kernel_times(plan)
+        samp_ms.append(a)
+        knn_ms.append(b)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_step = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    rho_ok = bool(torch.isfinite(rho_dev).all().item())
+
+    # End to end through the public API with pinned host buffers.
+    plan_h = ccm.plan_problem(ctx, p, 0)
+    s_host = torch.from_numpy(p.series).pin_memory().numpy()
+    rho_host = torch.zeros(ccm.rho_shape(p), dtype=torch.float64).pin_memory().numpy()
+    ccm.ccm_run(plan_h, s_host, rho_host)
+    e2e_s = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        ccm.ccm_run(plan_h, s_host, rho_host)     # H2D, graph, D2H, synchronise
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_t = sum(e2e_s) / len(e2e_s)
+    if dist:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    same = bool(np.array_equal(rho_host, rho_dev.cpu().numpy()))
+    ccm.ccm_plan_destroy(plan_h)
+
+    out = None
+    if rank == 0:
+        n_units = info["n_units"]
+        knn = sum(knn_ms) / len(knn_ms)
+        achieved = info["flop_count"] / (knn / 1e3) / 1e12
+        out = {
+            "metric": METRIC, "value": n_units * world / (t_step / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(), l2="256 MiB buffer written between timed steps",
+                           parallelism="replicas" if world > 1 else "single GPU"),
+            "queries_per_s": info["n_queries"] * world / (t_step / 1e3),
+            "pairs_per_s": info["pair_count"] * world / (t_step / 1e3),
+            "kernel_ms": {"sampler": sum(samp_ms) / len(samp_ms), "knn_fused": knn},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": traffic_entry(),
+                         "kernel": "knn_fused (3E FP32 flops per query-library pair)",
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "e2e": {"value": n_units * world / e2e_t, "unit": UNIT,
+                    "h2d_bytes_per_step": int(p.series.nbytes),
+                    "d2h_bytes_per_step": int(rho_host.nbytes),
+                    "ms_per_step": e2e_t * 1e3, "same_rho_as_device_path": same},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "rho_finite": rho_ok,
+        }
+        if not args.no_plain:
+            out["vs_plain_gpu"] = compare_plain(ccm, ctx, I, p, torch)
+    ccm.ccm_plan_destroy(plan)
+    ccm.ccm_context_destroy(ctx)
+    return out
+
+
+def compare_plain(ccm, ctx, I, p, torch):
+    """Fused sweep vs the plain one-launch-per-realization CCM on the same subset."""
+    import numpy as np
+    sub = I.subproblem(p, r=2)
+    flags = ccm.CCM_INPUT_ON_DEVICE | ccm.CCM_OUTPUT_ON_DEVICE
+    plan = ccm.plan_problem(ctx, sub, flags)
+    s = torch.from_numpy(sub.series).cuda()
+    ra = torch.zeros(ccm.rho_shape(sub), dtype=torch.float64, device="cuda")
+    rb = torch.zeros_like(ra)
+    st = torch.cuda.Stream()
+    ccm.ccm_run(plan, s, ra, stream=st)
+    ccm.ccm_run_plain(plan, s, rb, stream=st)
+    st.synchronize()
+    t0 = time.perf_counter()
+    ccm.ccm_run(plan, s, ra, stream=st)
+    st.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ccm.ccm_run_plain(plan, s, rb, stream=st)
+    st.synchronize()
+    tp = time.perf_counter() - t0
+    ccm.ccm_plan_destroy(plan)
+    n = sub.n_units()
+    return {"subset": "every (pair, E, tau, L) cell of the sweep with r=2 (3200 realizations)",
+            "fused_realizations_per_s": n / tf, "plain_realizations_per_s": n / tp,
+            "speedup": tp / tf,
+            "max_abs_rho_diff": float((ra - rb).abs().max().item())}
+
+
+def profile_case(r: int):
+    """Every sweep cell with r realizations, ccm_run twice (graph path)."""
+    import numpy as np
+    from paper_1905_00565_gb300 import ccm
+    from paper_1905_00565_gb300 import inputs as I
+    p = I.subproblem(I.sweep_problem(), r=r)
+    ctx = ccm.ccm_context_create(0)
+    plan = ccm.plan_problem(ctx, p)
+    rho = np.zeros(ccm.rho_shape(p))
+    for _ in range(2):
+        ccm.ccm_run(plan, p.series, rho)
+    print(json.dumps({"profile_case_r": r, "realizations": p.n_units(),
+                      "kernel_ms": ccm.ccm_plan_kernel_times(plan),
+                      "flops": ccm.ccm_plan_get_info(plan)["flop_count"]}))
+    ccm.ccm_plan_destroy(plan)
+    ccm.ccm_context_destroy(ctx)
+
+
+def main():
+    args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1905_00565_gb300 import inputs as I
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        p = I.sweep_problem()
+        for _ in range(args.warmup):
+            time_cpu_oracle(p, 16)
+        vals = [time_cpu_oracle(p, args.cpu_sample_units) for _ in range(args.steps)]
+        v = statistics.mean(x["value"] for x in vals)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * p.n_units() / v, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(),
+                "cpu_baseline": dict(vals[-1], value=v),
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    # the CPU baseline runs before any GPU work so that its spawned workers start clean
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = time_cpu_oracle(I.sweep_problem(), args.cpu_sample_units)
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,11 @@ ccm_status ccm_run(ccm_plan_t* plan, const float* series, double* rho, void* cud
 ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho,
                       const ccm_debug_out* dbg, void* cuda_stream);
 
+/* Device time of the sampler launch and of the fused kNN launch in the plan's
+ * last completed ccm_run / ccm_run_ex (CUDA events recorded on the run's
+ * stream around each launch).  Call after that run has finished. */
+ccm_status ccm_plan_kernel_times(const ccm_plan_t* plan, double* sampler_ms, double* knn_ms);
+
 /* The plain comparator: one sampler launch and one naive kNN launch per
  * realization (thread per query, library read from global memory, sorted
  * insertion), same precision and same results.  It exists to measure the

@@ -41,7 +41,8 @@ STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM
 # Every function the header declares, for the export check.
 EXPORTED = ["ccm_context_create", "ccm_context_destroy", "ccm_plan", "ccm_plan_destroy",
             "ccm_plan_get_info", "ccm_run", "ccm_run_ex", "ccm_run_plain", "ccm_submit",
-            "ccm_poll", "ccm_cancel", "ccm_job_times", "ccm_last_error", "ccm_version"]
+            "ccm_poll", "ccm_cancel", "ccm_job_times", "ccm_last_error", "ccm_version",
+            "ccm_plan_kernel_times"]
 
 
 class ccm_problem(ctypes.Structure):
@@ -87,6 +88,8 @@ def _load():
         "ccm_run": ([vp, vp, vp, vp], st),
         "ccm_run_ex": ([vp, vp, vp, ctypes.POINTER(ccm_debug_out), vp], st),
         "ccm_run_plain": ([vp, vp, vp, vp], st),
+        "ccm_plan_kernel_times": ([vp, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)], st),
         "ccm_submit": ([vp, ctypes.POINTER(ccm_problem), vp, ctypes.POINTER(u64)], st),
         "ccm_poll": ([vp, u64, vp, i32], st),
         "ccm_cancel": ([vp, u64], st),
@@ -199,6 +202,13 @@ def ccm_run_ex(plan: int, series, rho, libraries=None, neighbours=None, predicti
     dbg = ccm_debug_out(_ptr(libraries) or None, _ptr(neighbours) or None,
                         _ptr(predictions) or None)
     _check(_lib.ccm_run_ex(plan, _ptr(series), _ptr(rho), ctypes.byref(dbg), _stream(stream)))
+
+
+def ccm_plan_kernel_times(plan: int):
+    """(sampler_ms, knn_ms) device times of the plan's last completed run."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ccm_plan_kernel_times(plan, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def ccm_run_plain(plan: int, series, rho, stream=None) -> None:

@@ -269,6 +269,7 @@ struct ccm_plan_s {
   char* d_arena = nullptr;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before sampler, before knn, after knn
   int grid = 0;
   std::mutex run_mu;
   ccm_plan_info info{};
@@ -303,19 +304,22 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
 // Enqueue sampler + fused kernel for a whole unit list on stream s.
 ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int grid, int persistent,
                          int32_t* dbg_lib, const int64_t* d_dbg_lib_off, int32_t* dbg_nbr,
-                         float* dbg_xhat, cudaStream_t s) {
+                         float* dbg_xhat, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, sizeof(uint32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
   SamplerParams sp = sampler_params(base, ar);
   sp.dbg_lib = dbg_lib;
   sp.dbg_lib_off = d_dbg_lib_off;
+  if (ev) CCM_CUDA(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
   CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
   KnnParams kp = knn_params(base, ar, ul, persistent);
   kp.dbg_nbr = dbg_nbr;
   kp.dbg_xhat = dbg_xhat;
   const int g = persistent ? grid : (int)ul.items.size();
+  if (ev) CCM_CUDA(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
   CCM_CUDA(launch_knn(kp, ul.emin, ul.emax, g, s));
+  if (ev) CCM_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
   return CCM_OK;
 }
 
@@ -384,6 +388,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
     return fail(CCM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
   e = cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreate(&pl->ev[q]);
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_arena + pl->ar.units, pl->ul.units.data(),
                    sizeof(UnitDesc) * pl->ul.units.size(), cudaMemcpyHostToDevice);
@@ -424,6 +429,8 @@ ccm_status ccm_plan_destroy(ccm_plan_t* plan) {
   if (plan->stream) cudaStreamSynchronize(plan->stream);
   if (plan->graph) cudaGraphExecDestroy(plan->graph);
   if (plan->stream) cudaStreamDestroy(plan->stream);
+  for (cudaEvent_t ev : plan->ev)
+    if (ev) cudaEventDestroy(ev);
   cudaFree(plan->d_arena);
   release(plan->ctx, plan->ar.total);
   delete plan;
@@ -471,7 +478,8 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
                                  : reinterpret_cast<float*>(t2 + align_up(lb, 256) + align_up(nb, 256)))
                       : nullptr;
     CCM_CUDA(cudaMemcpyAsync(d_off, lib_off.data(), ob, cudaMemcpyHostToDevice, s));
-    ccm_status st = enqueue_sweep(base, plan->ar, ul, plan->grid, 1, d_lib, d_off, d_nbr, d_xh, s);
+    ccm_status st =
+        enqueue_sweep(base, plan->ar, ul, plan->grid, 1, d_lib, d_off, d_nbr, d_xh, s, plan->ev);
     if (st != CCM_OK) return st;
     if (!out_dev) {
       if (dbg->libraries) CCM_CUDA(cudaMemcpyAsync(dbg->libraries, d_lib, lb, cudaMemcpyDeviceToHost, s));
@@ -484,7 +492,7 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
       cudaGraph_t graph = nullptr;
       CCM_CUDA(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
       ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->grid, 1, nullptr, nullptr,
-                                    nullptr, nullptr, plan->stream);
+                                    nullptr, nullptr, plan->stream, plan->ev);
       const cudaError_t ce = cudaStreamEndCapture(plan->stream, &graph);
       if (st != CCM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -501,6 +509,17 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
   CCM_CUDA(cudaMemcpyAsync(rho, base + plan->ar.rho, rho_bytes,
                            out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   if (!cuda_stream || !in_dev || !out_dev) return check_err_flag(base, plan->ar, s);
+  return CCM_OK;
+}
+
+ccm_status ccm_plan_kernel_times(const ccm_plan_t* plan, double* sampler_ms, double* knn_ms) {
+  if (!plan) return fail(CCM_EINVAL, "plan is NULL");
+  CCM_CUDA(cudaSetDevice(plan->ctx->device));
+  float a = 0.f, b = 0.f;
+  CCM_CUDA(cudaEventElapsedTime(&a, plan->ev[0], plan->ev[1]));
+  CCM_CUDA(cudaEventElapsedTime(&b, plan->ev[1], plan->ev[2]));
+  if (sampler_ms) *sampler_ms = a;
+  if (knn_ms) *knn_ms = b;
   return CCM_OK;
 }
 
