@@ -304,22 +304,29 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
 // Enqueue sampler + fused kernel for a whole unit list on stream s.
 ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int grid, int persistent,
                          int32_t* dbg_lib, const int64_t* d_dbg_lib_off, int32_t* dbg_nbr,
-                         float* dbg_xhat, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+                         float* dbg_xhat, cudaStream_t s, cudaEvent_t* ev = nullptr,
+                         bool capturing = false) {
+  // Inside stream capture an event record becomes a graph node only with the
+  // external flag; outside capture the plain record is the valid form.
+  auto record = [&](cudaEvent_t e) {
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                     : cudaEventRecord(e, s);
+  };
   CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, sizeof(uint32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
   SamplerParams sp = sampler_params(base, ar);
   sp.dbg_lib = dbg_lib;
   sp.dbg_lib_off = d_dbg_lib_off;
-  if (ev) CCM_CUDA(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
+  if (ev) CCM_CUDA(record(ev[0]));
   CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
   KnnParams kp = knn_params(base, ar, ul, persistent);
   kp.dbg_nbr = dbg_nbr;
   kp.dbg_xhat = dbg_xhat;
   const int g = persistent ? grid : (int)ul.items.size();
-  if (ev) CCM_CUDA(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
+  if (ev) CCM_CUDA(record(ev[1]));
   CCM_CUDA(launch_knn(kp, ul.emin, ul.emax, g, s));
-  if (ev) CCM_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
+  if (ev) CCM_CUDA(record(ev[2]));
   return CCM_OK;
 }
 
@@ -492,7 +499,7 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
       cudaGraph_t graph = nullptr;
       CCM_CUDA(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
       ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->grid, 1, nullptr, nullptr,
-                                    nullptr, nullptr, plan->stream, plan->ev);
+                                    nullptr, nullptr, plan->stream, plan->ev, true);
       const cudaError_t ce = cudaStreamEndCapture(plan->stream, &graph);
       if (st != CCM_OK) {
         if (graph) cudaGraphDestroy(graph);
