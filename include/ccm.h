@@ -170,6 +170,28 @@ ccm_status ccm_cancel(ccm_context* ctx, uint64_t ticket);
 ccm_status ccm_job_times(ccm_context* ctx, uint64_t ticket, double* submit_s, double* start_s,
                          double* finish_s);
 
+/* One CCM cell without any device allocation (the paper has no counterpart:
+ * it exists for callers that cannot call cudaMalloc at run time, e.g. a host
+ * framework whose own caching allocator owns the device memory, or a
+ * latency-critical loop where cudaMalloc/cudaFree may synchronise the device).
+ * Computes rho of pair (j, i), E, tau, L for realizations k = 0..r-1 with the
+ * same sampler and fused kernel as ccm_run, so d_rho[k] equals the matching
+ * entry of ccm_run's output for the same seed.
+ * d_series: device [n_series][n] FP32 (not checked for non-finite values);
+ * d_rho: device [r] FP64, written in stream order.  All scratch lives in one
+ * fixed 16 MiB device array held by every GPU that loads the library until
+ * exit; a cell needing more (about r*L*4 + r*ceil(N_m/512)*56 + r*100 bytes)
+ * returns CCM_ETOOLARGE with a message and runs nothing.  Nothing is
+ * allocated.  The first call on a device (with that device current) finds
+ * the array's address and sets kernel attributes; make it before any stream
+ * capture.  Every call reuses the same array: calls that overlap on the GPU
+ * (several streams or host threads) race and must be serialised by the
+ * caller.  cuda_stream NULL: runs on the default stream and blocks until done,
+ * then reports kernel error flags; otherwise asynchronous. */
+ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, int64_t n, int32_t j,
+                           int32_t i, int32_t E, int32_t tau, int64_t L, int32_t r,
+                           uint64_t seed, double* d_rho, void* cuda_stream);
+
 /* Thread-local message describing the last non-OK status on this thread. */
 const char* ccm_last_error(void);
 

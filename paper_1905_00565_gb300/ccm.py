@@ -42,7 +42,7 @@ STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM
 EXPORTED = ["ccm_context_create", "ccm_context_destroy", "ccm_plan", "ccm_plan_destroy",
             "ccm_plan_get_info", "ccm_run", "ccm_run_ex", "ccm_run_plain", "ccm_submit",
             "ccm_poll", "ccm_cancel", "ccm_job_times", "ccm_last_error", "ccm_version",
-            "ccm_plan_kernel_times"]
+            "ccm_plan_kernel_times", "ccm_run_noalloc"]
 
 
 class ccm_problem(ctypes.Structure):
@@ -95,6 +95,7 @@ def _load():
         "ccm_cancel": ([vp, u64], st),
         "ccm_job_times": ([vp, u64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], st),
+        "ccm_run_noalloc": ([vp, i32, i64, i32, i32, i32, i32, i64, i32, u64, vp, vp], st),
         "ccm_last_error": ([], ctypes.c_char_p),
         "ccm_version": ([], ctypes.c_char_p),
     }
@@ -238,6 +239,15 @@ def ccm_job_times(ctx: int, ticket: int):
     st = _check(_lib.ccm_job_times(ctx, int(ticket), ctypes.byref(a), ctypes.byref(b),
                                    ctypes.byref(c)))
     return st, a.value, b.value, c.value
+
+
+def ccm_run_noalloc(d_series, j: int, i: int, E: int, tau: int, L: int, r: int, seed: int,
+                    d_rho, stream=None) -> None:
+    """One cell into device ``d_rho`` [r] from device ``d_series`` [V][n], with no
+    device allocation (all scratch in the library's fixed device array)."""
+    V, n = int(d_series.shape[0]), int(d_series.shape[1])
+    _check(_lib.ccm_run_noalloc(_ptr(d_series), V, n, int(j), int(i), int(E), int(tau), int(L),
+                                int(r), int(seed), _ptr(d_rho), _stream(stream)))
 
 
 def plan_problem(ctx: int, problem, flags: int = 0) -> int:

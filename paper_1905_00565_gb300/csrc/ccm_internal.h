@@ -77,6 +77,9 @@ cudaError_t knn_prepare();
 cudaError_t knn_occupancy(int emin, int emax, int* ctas_per_sm);
 cudaError_t launch_knn(const KnnParams& p, int emin, int emax, int grid, cudaStream_t s);
 
+// Sets the thread-local message returned by ccm_last_error() (runtime.cu).
+void set_last_error(const char* msg);
+
 // Plain comparator (plain.cu): one realization per call.
 cudaError_t launch_plain_unit(const float* series, const UnitDesc* unit_dev, const UnitDesc& unit,
                               const int32_t* lib, float* xhat_scratch, double* rho_out,

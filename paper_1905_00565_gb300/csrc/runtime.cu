@@ -215,6 +215,10 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
 
 }  // namespace
 
+namespace ccm {
+void set_last_error(const char* msg) { t_err = msg; }
+}  // namespace ccm
+
 // ================================================================ context ===
 struct Job;
 struct Batch;
