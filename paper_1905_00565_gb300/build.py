@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libccm_gb300.so")
-SOURCES = ["runtime.cu", "sampler.cu", "knn_fused.cu", "plain.cu", "noalloc.cu"]
+SOURCES = ["runtime.cu", "sampler.cu", "knn_fused.cu", "plain.cu", "noalloc.cu", "order.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,6 +35,7 @@ def _compile(src: str, verbose: bool) -> str:
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+           *os.environ.get("CCM_EXTRA_NVCC_FLAGS", "").split(),
            "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

@@ -18,6 +18,7 @@ struct UnitDesc {
   int64_t q_off;        // first query of this unit in the concatenated debug outputs
   int64_t nbr_off;      // first neighbour entry in the concatenated debug outputs
   int64_t out_idx;      // index of this unit's rho in the rho buffer
+  int64_t order_off;    // first entry of this unit's query order (per variable, E, tau)
   uint64_t seed;        // library sampler seed of the job
   int32_t j, i;         // library variable, target variable
   int32_t E, tau;
@@ -31,6 +32,15 @@ struct WorkItem {
   int32_t unit;
   int32_t tile;
 };
+
+// Query order job: one per (job, library variable, E, tau).
+struct OrderJob {
+  int64_t series_off;   // element offset of the job's series block
+  int64_t n;            // series length
+  int64_t order_off;    // first entry of the order array of this combination
+  int32_t j, E, tau, n_m;
+};
+constexpr int kOrderMaxSort = 16384;   // manifolds up to this size are sorted
 
 // Sampler: one CTA per unit.
 struct SamplerParams {
@@ -48,6 +58,7 @@ struct KnnParams {
   const WorkItem* items;
   int64_t n_items;
   const int32_t* lib;
+  const int32_t* order;   // query order (manifold index per position)
   double* partials;       // 6 doubles per query tile
   uint32_t* unit_done;    // per-unit tile counters (reset by the unit's last tile)
   uint32_t* item_counter; // dynamic scheduling counter (zeroed before each launch)
@@ -56,7 +67,11 @@ struct KnnParams {
   float* dbg_xhat;        // optional [sum N_m]
   int32_t* err;
   int32_t persistent;     // 1: CTAs pull items from item_counter; 0: item = blockIdx.x
+  int32_t merge_at[kMaxE + 1];  // per E: merge pending candidates once a lane holds this many
 };
+
+// Default merge trigger per E (pending candidates per lane), before tuning.
+constexpr int kDefaultMergeAt = 9;
 
 // Error flag values written by kernels.
 constexpr int32_t kErrBadUnit = 1;
@@ -68,6 +83,11 @@ constexpr int kSamplerSmemKeys = 40960;   // keys kept in shared memory up to th
 cudaError_t sampler_prepare();
 cudaError_t launch_sampler(const SamplerParams& p, int64_t first_unit, int64_t count,
                            int max_nm, cudaStream_t s);
+
+// Query order (order.cu).
+cudaError_t order_prepare();
+cudaError_t launch_order(const float* series, const OrderJob* jobs, int64_t n_jobs, int max_nm,
+                         int32_t* order, cudaStream_t s);
 
 // Fused kernel (knn_fused.cu).
 int knn_block_threads();

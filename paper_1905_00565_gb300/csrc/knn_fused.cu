@@ -41,20 +41,43 @@ namespace {
 
 using u64 = unsigned long long;
 
-constexpr int kThreads = 256;             // threads per CTA
-constexpr int kQ = 2;                     // queries per thread (one packed f32x2 pair)
-constexpr int kQT = kThreads * kQ;        // queries per tile
-constexpr int kBuf = 8;                   // pending candidates per query
-constexpr int kCoordBytes = 64 * 1024;    // shared memory for one library tile
-constexpr int kBufBytes = kBuf * kQ * kThreads * 8;
+constexpr int kThreads = 256;             // threads per CTA = queries per tile
+constexpr int kQT = kThreads;             // queries per tile (one per thread)
+constexpr int kBuf = 16;                  // pending candidates per query
+constexpr int kCoordBytes = 40 * 1024;    // shared memory for one library tile
+#ifndef CCM_STEP_SMALL_E
+#define CCM_STEP_SMALL_E 8
+#endif
+#ifndef CCM_STEP_LARGE_E
+#define CCM_STEP_LARGE_E 4
+#endif
+#ifndef CCM_STEP_SPLIT_E
+#define CCM_STEP_SPLIT_E 6
+#endif
+#ifndef CCM_EARLY_MIN_E
+#define CCM_EARLY_MIN_E 3
+#endif
+// Library points per step (two points per packed operand): more points give
+// more independent FMA chains per warp; large E is limited by registers.
+template <int E>
+constexpr int kStepE = (E <= CCM_STEP_SPLIT_E) ? CCM_STEP_SMALL_E : CCM_STEP_LARGE_E;
+constexpr int kBufBytes = kBuf * kThreads * 8;
 constexpr int kSmemBytes = kCoordBytes + kBufBytes;
 constexpr unsigned kFull = 0xffffffffu;
 
+#ifndef CCM_EARLY_MAX_E
+#define CCM_EARLY_MAX_E 6
+#endif
+// Coordinates summed before the early-termination check (E when there is none).
+template <int E>
+constexpr int kE1 = (E < CCM_EARLY_MIN_E || E > CCM_EARLY_MAX_E || E <= 2) ? E : 2;
+
 template <int E>
 struct TileShape {
-  static constexpr int EP = E + (E & 1);                              // coordinates padded to even
-  static constexpr int LT = (kCoordBytes / (EP * 8 + 4)) & ~63;       // library points per tile
-  static_assert(LT >= 64, "tile too small");
+  static constexpr int EP = E + (E & 1);                        // coordinates padded to even
+  // library points per tile: a point pair takes EP*8 bytes of coordinates + 8 of indices
+  static constexpr int LT = (kCoordBytes / (EP * 8 + 8)) * 2 / 64 * 64;
+  static_assert(LT >= 64 && LT % kStepE<E> == 0, "tile must hold whole steps");
 };
 
 __device__ __forceinline__ u64 pack2(float a, float b) {
@@ -81,23 +104,45 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
   return r;
 }
 
-// Squared distances of the two packed queries to one library point whose
-// duplicated coordinates start at `c` (16-byte aligned, EP entries).
-template <int E>
-__device__ __forceinline__ u64 sqdist2(const u64 (&qc)[E], const u64* c) {
+// Squared distances of one query (coordinates duplicated, {q_e, q_e}) to a
+// pair of library points whose coordinates are packed {a_e, b_e} starting at
+// `c` (16-byte aligned, EP entries): {d2(q, a), d2(q, b)}, accumulated over
+// coordinates [EB, EE) onto `acc` in the fixed order (coordinate 0 a rounded
+// product, every later one a fused multiply-add).  Calling it for [0, E1)
+// and then [E1, E) gives exactly the bits of one call for [0, E).
+template <int E, int EB, int EE>
+__device__ __forceinline__ u64 sqdist2_range(const u64 (&qc)[E], const u64* c, u64 acc) {
   const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(c);
-  u64 acc = 0;
 #pragma unroll
-  for (int e = 0; e < E; e += 2) {
+  for (int e = EB & ~1; e < EE; e += 2) {
     const ulonglong2 v = c2[e / 2];
-    const u64 d0 = sub2(qc[e], v.x);
-    acc = (e == 0) ? mul2(d0, d0) : fma2(d0, d0, acc);
-    if (e + 1 < E) {
+    if (e >= EB) {
+      const u64 d0 = sub2(qc[e], v.x);
+      acc = (e == 0) ? mul2(d0, d0) : fma2(d0, d0, acc);
+    }
+    if (e + 1 < EE && e + 1 >= EB) {
       const u64 d1 = sub2(qc[e + 1], v.y);
       acc = fma2(d1, d1, acc);
     }
   }
   return acc;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Smallest of N distances (three-input min where possible).
+template <int N>
+__device__ __forceinline__ float min_all(const float (&d)[N]) {
+  float m = d[0];
+  int i = 1;
+#pragma unroll
+  for (; i + 1 < N; i += 2) m = min3f(m, d[i], d[i + 1]);
+  if (i < N) m = fminf(m, d[i]);
+  return m;
 }
 
 // Insert (x, lx) into the ascending list kd[0..K), keeping entries that are
@@ -156,9 +201,9 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   constexpr int K = E + 2;
   constexpr int EP = TileShape<E>::EP;
   constexpr int LT = TileShape<E>::LT;
-  u64* s_coord = reinterpret_cast<u64*>(smem);                              // [LT][EP]
-  int32_t* s_lidx = reinterpret_cast<int32_t*>(smem + (size_t)LT * EP * 8);  // [LT]
-  int2* s_buf = reinterpret_cast<int2*>(smem + kCoordBytes);                // [kBuf][kQ][kThreads]
+  u64* s_coord = reinterpret_cast<u64*>(smem);                                   // [LT/2][EP]
+  int32_t* s_lidx = reinterpret_cast<int32_t*>(smem + (size_t)(LT / 2) * EP * 8);  // [LT]
+  int2* s_buf = reinterpret_cast<int2*>(smem + kCoordBytes);                     // [kBuf][kThreads]
 
   const int tid = threadIdx.x;
   const int n_m = u.n_m, L = u.L, tau = u.tau;
@@ -166,146 +211,142 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
   const float* si = p.series + u.series_off + (int64_t)u.i * u.n;
   const int32_t* lib = p.lib + u.lib_off;
+  const int32_t* order = p.order + u.order_off;
+  constexpr int kStep = kStepE<E>;
+  constexpr int kPairs = kStep / 2;
+  // merge trigger: at most kBuf - kStep + 1 so that a step can always append
+  const int merge_at = max(1, min(p.merge_at[E], kBuf - kStep + 1));
 
-  int m[kQ];
-  bool valid[kQ];
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    m[q] = tile * kQT + q * kThreads + tid;
-    valid[q] = m[q] < n_m;
-    if (!valid[q]) m[q] = n_m - 1;
-  }
+  // A warp's 32 queries are consecutive positions of the query order.
+  const int pos = tile * kQT + tid;
+  const bool valid = pos < n_m;
+  const int m = order[valid ? pos : n_m - 1];
   u64 qc[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) qc[e] = pack2(sj[m[0] + off - e * tau], sj[m[1] + off - e * tau]);
+  for (int e = 0; e < E; ++e) {
+    const float c = sj[m + off - e * tau];
+    qc[e] = pack2(c, c);
+  }
 
-  float kd[kQ][K];
-  int kl[kQ][K];
+  float kd[K];
+  int kl[K];
 #pragma unroll
-  for (int q = 0; q < kQ; ++q)
-#pragma unroll
-    for (int s = 0; s < K; ++s) {
-      kd[q][s] = INFINITY;
-      kl[q][s] = -1;
-    }
-  int cnt[kQ] = {0, 0};
+  for (int s = 0; s < K; ++s) {
+    kd[s] = INFINITY;
+    kl[s] = -1;
+  }
+  int cnt = 0;
 
   auto merge_all = [&]() {
-    int mx = max(cnt[0], cnt[1]);
-    mx = (int)__reduce_max_sync(kFull, (unsigned)mx);
+    const int mx = (int)__reduce_max_sync(kFull, (unsigned)cnt);
     for (int b = 0; b < mx; ++b) {
-#pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        if (b < cnt[q]) {
-          const int2 v = s_buf[(b * kQ + q) * kThreads + tid];
-          insert_sorted<K>(kd[q], kl[q], __int_as_float(v.x), v.y);
-        }
+      if (b < cnt) {
+        const int2 v = s_buf[b * kThreads + tid];
+        insert_sorted<K>(kd, kl, __int_as_float(v.x), v.y);
       }
     }
-    cnt[0] = 0;
-    cnt[1] = 0;
+    cnt = 0;
   };
 
   for (int t0 = 0; t0 < L; t0 += LT) {
     const int nt = min(LT, L - t0);
-    const int ntp = (nt + 1) & ~1;
+    const int ntp = (nt + kStep - 1) / kStep * kStep;
     __syncthreads();  // the previous tile has been consumed
     for (int a = tid; a < ntp; a += kThreads) {
+      const int pp = a >> 1, half = a & 1;
+      float* cpair = reinterpret_cast<float*>(s_coord + (size_t)pp * EP);
       if (a < nt) {
         const int l = lib[t0 + a];
         s_lidx[a] = l;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const float c = sj[l + off - e * tau];
-          s_coord[a * EP + e] = pack2(c, c);
-        }
+        for (int e = 0; e < E; ++e) cpair[2 * e + half] = sj[l + off - e * tau];
       } else {  // sentinel point: infinite distance, never selected
         s_lidx[a] = 0x7fffffff;
 #pragma unroll
-        for (int e = 0; e < E; ++e) s_coord[a * EP + e] = pack2(INFINITY, INFINITY);
+        for (int e = 0; e < E; ++e) cpair[2 * e + half] = INFINITY;
       }
-      if (EP > E) s_coord[a * EP + E] = 0ull;
+      if (EP > E) cpair[2 * E + half] = 0.f;
     }
     __syncthreads();
 
 #pragma unroll 1
-    for (int a = 0; a < ntp; a += 2) {
-      const u64 r0 = sqdist2<E>(qc, s_coord + (size_t)a * EP);
-      const u64 r1 = sqdist2<E>(qc, s_coord + (size_t)(a + 1) * EP);
-      float d00, d10, d01, d11;  // d[query][point]
-      unpack2(r0, d00, d10);
-      unpack2(r1, d01, d11);
-      const float th0 = kd[0][K - 1], th1 = kd[1][K - 1];
-      const bool pass = (d00 < th0) | (d01 < th0) | (d10 < th1) | (d11 < th1);
-      if (__any_sync(kFull, pass)) {
-        const int l0 = s_lidx[a], l1 = s_lidx[a + 1];
-        if (d00 < th0) { s_buf[(cnt[0] * kQ + 0) * kThreads + tid] = make_int2(__float_as_int(d00), l0); ++cnt[0]; }
-        if (d01 < th0) { s_buf[(cnt[0] * kQ + 0) * kThreads + tid] = make_int2(__float_as_int(d01), l1); ++cnt[0]; }
-        if (d10 < th1) { s_buf[(cnt[1] * kQ + 1) * kThreads + tid] = make_int2(__float_as_int(d10), l0); ++cnt[1]; }
-        if (d11 < th1) { s_buf[(cnt[1] * kQ + 1) * kThreads + tid] = make_int2(__float_as_int(d11), l1); ++cnt[1]; }
-        const bool need = (cnt[0] > kBuf - 2) | (cnt[1] > kBuf - 2);
-        if (__any_sync(kFull, need)) merge_all();
+    for (int a = 0; a < ntp; a += kStep) {
+      const u64* cp = s_coord + (size_t)(a >> 1) * EP;
+      // Partial sums over the first E1 coordinates are lower bounds of the
+      // full FP32 sums (all terms are >= 0 and rounding is monotone), so a
+      // step whose partials are all at or above every lane's threshold cannot
+      // contribute a candidate and skips the remaining coordinates.
+      u64 r[kPairs];
+#pragma unroll
+      for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, kE1<E>>(qc, cp + pp * EP, 0ull);
+      const float th = kd[K - 1];
+      float d[kStep];
+#pragma unroll
+      for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+      if (!__any_sync(kFull, min_all(d) < th)) continue;
+      if constexpr (kE1<E> < E) {
+#pragma unroll
+        for (int pp = 0; pp < kPairs; ++pp) {
+          r[pp] = sqdist2_range<E, kE1<E>, E>(qc, cp + pp * EP, r[pp]);
+          unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+        }
+        if (!__any_sync(kFull, min_all(d) < th)) continue;
       }
+#pragma unroll
+      for (int pt = 0; pt < kStep; ++pt) {
+        if (d[pt] < th) {
+          s_buf[cnt * kThreads + tid] = make_int2(__float_as_int(d[pt]), s_lidx[a + pt]);
+          ++cnt;
+        }
+      }
+      if (__any_sync(kFull, cnt >= merge_at)) merge_all();
     }
   }
   merge_all();
 
   // Epilogue: drop the query itself, simplex weights, prediction, moments.
-  double xo[kQ], xp[kQ];
+  int self = K;
 #pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    int self = K;
+  for (int s = 0; s < K; ++s) self = (kl[s] == m && self == K) ? s : self;
+  float dd[E + 1];
+  int nb[E + 1];
 #pragma unroll
-    for (int s = 0; s < K; ++s) self = (kl[q][s] == m[q] && self == K) ? s : self;
-    float dd[E + 1];
-    int nb[E + 1];
+  for (int s = 0; s <= E; ++s) {
+    dd[s] = (s < self) ? kd[s] : kd[s + 1];
+    nb[s] = (s < self) ? kl[s] : kl[s + 1];
+  }
+  const float d1 = sqrtf(dd[0]);
+  float usum = 0.f, acc = 0.f;
 #pragma unroll
-    for (int s = 0; s <= E; ++s) {
-      dd[s] = (s < self) ? kd[q][s] : kd[q][s + 1];
-      nb[s] = (s < self) ? kl[q][s] : kl[q][s + 1];
-    }
-    const float d1 = sqrtf(dd[0]);
-    float usum = 0.f, acc = 0.f;
+  for (int s = 0; s <= E; ++s) {
+    const float di = sqrtf(dd[s]);
+    const float ui = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
+    usum += ui;
+    // an unfilled slot (only possible with non-finite device input) reads in bounds
+    const int nbc = min(max(nb[s], 0), n_m - 1);
+    acc = fmaf(ui, si[nbc + off], acc);
+  }
+  const float xhat = acc / usum;
+  const double xo = valid ? (double)si[m + off] : 0.0;
+  const double xp = valid ? (double)xhat : 0.0;
+  if (valid) {
+    if (p.dbg_xhat) p.dbg_xhat[u.q_off + m] = xhat;
+    if (p.dbg_nbr) {
 #pragma unroll
-    for (int s = 0; s <= E; ++s) {
-      const float di = sqrtf(dd[s]);
-      const float ui = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
-      usum += ui;
-      // an unfilled slot (only possible with non-finite device input) reads in bounds
-      const int nbc = min(max(nb[s], 0), n_m - 1);
-      acc = fmaf(ui, si[nbc + off], acc);
-    }
-    const float xhat = acc / usum;
-    xo[q] = valid[q] ? (double)si[m[q] + off] : 0.0;
-    xp[q] = valid[q] ? (double)xhat : 0.0;
-    if (valid[q]) {
-      if (p.dbg_xhat) p.dbg_xhat[u.q_off + m[q]] = xhat;
-      if (p.dbg_nbr) {
-#pragma unroll
-        for (int s = 0; s <= E; ++s) p.dbg_nbr[u.nbr_off + (int64_t)m[q] * (E + 1) + s] = nb[s];
-      }
+      for (int s = 0; s <= E; ++s) p.dbg_nbr[u.nbr_off + (int64_t)m * (E + 1) + s] = nb[s];
     }
   }
 
   // Tile moments, two passes over the registers.
-  double n = 0.0, sx = 0.0, sy = 0.0;
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    n += valid[q] ? 1.0 : 0.0;
-    sx += xo[q];
-    sy += xp[q];
-  }
+  double n = valid ? 1.0 : 0.0, sx = xo, sy = xp;
   block_sum3(n, sx, sy, s_red);
   const double mx = sx / n, my = sy / n;
   double sxx = 0.0, syy = 0.0, sxy = 0.0;
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    if (valid[q]) {
-      const double a = xo[q] - mx, b = xp[q] - my;
-      sxx += a * a;
-      syy += b * b;
-      sxy += a * b;
-    }
+  if (valid) {
+    const double a = xo - mx, b = xp - my;
+    sxx = a * a;
+    syy = b * b;
+    sxy = a * b;
   }
   block_sum3(sxx, syy, sxy, s_red);
 
@@ -327,15 +368,15 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
       double SXX = __ldcg(base + 3), SYY = __ldcg(base + 4), SXY = __ldcg(base + 5);
       for (int t = 1; t < u.n_tiles; ++t) {
         const double* pt = base + 6 * t;
-        const double nb = __ldcg(pt + 0), mxb = __ldcg(pt + 1), myb = __ldcg(pt + 2);
-        const double tot = N + nb;
+        const double nb2 = __ldcg(pt + 0), mxb = __ldcg(pt + 1), myb = __ldcg(pt + 2);
+        const double tot = N + nb2;
         const double dx = mxb - MX, dy = myb - MY;
-        const double f = N * nb / tot;
+        const double f = N * nb2 / tot;
         SXX += __ldcg(pt + 3) + dx * dx * f;
         SYY += __ldcg(pt + 4) + dy * dy * f;
         SXY += __ldcg(pt + 5) + dx * dy * f;
-        MX += dx * nb / tot;
-        MY += dy * nb / tot;
+        MX += dx * nb2 / tot;
+        MY += dy * nb2 / tot;
         N = tot;
       }
       p.rho[u.out_idx] = (SXX > 0.0 && SYY > 0.0) ? SXY / sqrt(SXX * SYY) : nan("");
@@ -364,7 +405,7 @@ __device__ __forceinline__ bool dispatch(int E, const KnnParams& p, const UnitDe
 }
 
 template <int EMIN, int EMAX>
-__global__ void __launch_bounds__(kThreads, 2) knn_fused_kernel(KnnParams p) {
+__global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double s_red[3 * (kThreads / 32) + 3];
   __shared__ int s_item, s_last;
@@ -405,7 +446,7 @@ cudaError_t occupancy_range(int* ctas) {
 }  // namespace
 
 int knn_block_threads() { return kThreads; }
-int knn_queries_per_thread() { return kQ; }
+int knn_queries_per_thread() { return 1; }
 size_t knn_smem_bytes(int, int) { return kSmemBytes; }
 
 // Instantiations: one kernel per single E (used when a plan has one E) and

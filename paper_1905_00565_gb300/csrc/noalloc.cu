@@ -30,19 +30,19 @@
 namespace ccm {
 
 // Scratch for one cell: descriptors, work items, libraries, partial moments,
-// counters.  16 MiB holds, e.g., r = 250 realizations of L = 9000 at N = 10^4.
+// counters, query order.  16 MiB holds, e.g., r = 250 realizations of L = 9000 at N = 10^4.
 constexpr size_t kScratchBytes = 16u << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
 struct NoallocLayout {
-  size_t units, items, lib, part, done, err, counter, total;
+  size_t units, items, lib, part, done, err, counter, order, orderjob, total;
 };
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-NoallocLayout noalloc_layout(int64_t r, int64_t L, int64_t n_tiles) {
+NoallocLayout noalloc_layout(int64_t r, int64_t L, int64_t n_tiles, int64_t n_m) {
   NoallocLayout a;
   size_t o = 0;
   a.units = o;
@@ -59,6 +59,10 @@ NoallocLayout noalloc_layout(int64_t r, int64_t L, int64_t n_tiles) {
   o = up256(o + sizeof(int32_t));
   a.counter = o;
   o = up256(o + sizeof(uint32_t));
+  a.order = o;
+  o = up256(o + sizeof(int32_t) * (size_t)n_m);
+  a.orderjob = o;
+  o = up256(o + sizeof(OrderJob));
   a.total = o;
   return a;
 }
@@ -91,6 +95,7 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     u.q_off = k * (int64_t)c.n_m;
     u.nbr_off = k * (int64_t)c.n_m * (c.E + 1);
     u.out_idx = k;
+    u.order_off = 0;
     u.seed = c.seed;
     u.j = c.j;
     u.i = c.i;
@@ -104,6 +109,15 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     done[k] = 0u;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    OrderJob oj;
+    oj.series_off = 0;
+    oj.n = c.n;
+    oj.order_off = 0;
+    oj.j = c.j;
+    oj.E = c.E;
+    oj.tau = c.tau;
+    oj.n_m = c.n_m;
+    *reinterpret_cast<OrderJob*>(scratch + lay.orderjob) = oj;
     *reinterpret_cast<int32_t*>(scratch + lay.err) = 0;
     *reinterpret_cast<uint32_t*>(scratch + lay.counter) = 0u;
   }
@@ -137,7 +151,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   if (r < 1) return noalloc_fail(CCM_EINVAL, "r must be >= 1");
   const int64_t tileq = (int64_t)knn_block_threads() * knn_queries_per_thread();
   const int64_t n_tiles = (n_m + tileq - 1) / tileq;
-  const NoallocLayout lay = noalloc_layout(r, L, n_tiles);
+  const NoallocLayout lay = noalloc_layout(r, L, n_tiles, n_m);
   if (lay.total > kScratchBytes)
     return noalloc_fail(CCM_ETOOLARGE,
                         "cell needs " + std::to_string(lay.total) + " B of scratch; the fixed "
@@ -152,6 +166,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
     if (!g_scratch_addr[dev]) {
       e = sampler_prepare();
       if (e == cudaSuccess) e = knn_prepare();
+      if (e == cudaSuccess) e = order_prepare();
       void* p = nullptr;
       if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess)
@@ -173,6 +188,9 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   c.n_m = (int32_t)n_m;
   c.n_tiles = (int32_t)n_tiles;
   noalloc_setup_kernel<<<(unsigned)((r * n_tiles + 255) / 256), 256, 0, s>>>(scratch, lay, c);
+  e = launch_order(d_series, reinterpret_cast<const OrderJob*>(scratch + lay.orderjob), 1,
+                   (int)n_m, reinterpret_cast<int32_t*>(scratch + lay.order), s);
+  if (e != cudaSuccess) return noalloc_fail(CCM_ECUDA, cudaGetErrorString(e));
   SamplerParams sp{};
   sp.units = reinterpret_cast<const UnitDesc*>(scratch + lay.units);
   sp.lib = reinterpret_cast<int32_t*>(scratch + lay.lib);
@@ -185,12 +203,14 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   kp.items = reinterpret_cast<const WorkItem*>(scratch + lay.items);
   kp.n_items = (int64_t)r * n_tiles;
   kp.lib = reinterpret_cast<const int32_t*>(scratch + lay.lib);
+  kp.order = reinterpret_cast<const int32_t*>(scratch + lay.order);
   kp.partials = reinterpret_cast<double*>(scratch + lay.part);
   kp.unit_done = reinterpret_cast<uint32_t*>(scratch + lay.done);
   kp.item_counter = reinterpret_cast<uint32_t*>(scratch + lay.counter);
   kp.rho = d_rho;
   kp.err = reinterpret_cast<int32_t*>(scratch + lay.err);
   kp.persistent = 0;
+  for (int q = 0; q <= kMaxE; ++q) kp.merge_at[q] = kDefaultMergeAt;
   e = launch_knn(kp, E, E, (int)kp.n_items, s);
   if (e != cudaSuccess) return noalloc_fail(CCM_ECUDA, cudaGetErrorString(e));
   if (!cuda_stream) {

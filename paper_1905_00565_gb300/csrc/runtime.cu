@@ -17,6 +17,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <list>
@@ -25,6 +26,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "ccm.h"
@@ -120,7 +122,8 @@ struct UnitList {
   std::vector<UnitDesc> units;
   std::vector<WorkItem> items;
   std::vector<double> item_cost;
-  int64_t lib_total = 0, part_total = 0, q_total = 0, nbr_total = 0;
+  std::vector<OrderJob> orders;  // one per (job, library variable, E, tau)
+  int64_t lib_total = 0, part_total = 0, q_total = 0, nbr_total = 0, order_total = 0;
   int emin = kMaxE + 1, emax = 0, max_nm = 0;
   double pairs = 0.0, flops = 0.0;
 };
@@ -130,6 +133,25 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
   const int tileq = knn_block_threads() * knn_queries_per_thread();
   const int64_t nP = (int64_t)pc.pairs.size() / 2;
   int64_t out = out_base;
+  std::map<std::tuple<int32_t, int32_t, int32_t>, int64_t> combo;  // (j, E, tau) -> order_off
+  for (int64_t p = 0; p < nP; ++p)
+    for (int32_t E : pc.E)
+      for (int32_t tau : pc.tau) {
+        const auto key = std::make_tuple(pc.pairs[2 * p], E, tau);
+        if (combo.count(key)) continue;
+        OrderJob oj;
+        std::memset(&oj, 0, sizeof(oj));
+        oj.series_off = series_off;
+        oj.n = pc.n;
+        oj.order_off = ul->order_total;
+        oj.j = pc.pairs[2 * p];
+        oj.E = E;
+        oj.tau = tau;
+        oj.n_m = (int32_t)(pc.n - (int64_t)(E - 1) * tau);
+        combo[key] = oj.order_off;
+        ul->order_total += oj.n_m;
+        ul->orders.push_back(oj);
+      }
   for (int64_t p = 0; p < nP; ++p)
     for (int32_t E : pc.E)
       for (int32_t tau : pc.tau)
@@ -153,6 +175,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
             u.q_off = ul->q_total;
             u.nbr_off = ul->nbr_total;
             u.out_idx = out++;
+            u.order_off = combo[std::make_tuple(u.j, E, tau)];
             const int32_t uidx = (int32_t)ul->units.size();
             for (int32_t t = 0; t < u.n_tiles; ++t) {
               const int64_t nq = std::min<int64_t>(tileq, u.n_m - (int64_t)t * tileq);
@@ -188,7 +211,7 @@ void sort_items(UnitList* ul) {
 // Device arena layout for a unit list.
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
-         counter = 0, scratch = 0, total = 0;
+         counter = 0, scratch = 0, order = 0, orders = 0, total = 0;
 };
 
 Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
@@ -209,6 +232,8 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.err = take(sizeof(int32_t));
   a.counter = take(sizeof(uint32_t));
   a.scratch = take(sizeof(float) * (size_t)scratch_floats);
+  a.order = take(sizeof(int32_t) * (size_t)ul.order_total);
+  a.orders = take(sizeof(OrderJob) * ul.orders.size());
   a.total = o;
   return a;
 }
@@ -296,12 +321,16 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.items = reinterpret_cast<const WorkItem*>(base + ar.items);
   kp.n_items = (int64_t)ul.items.size();
   kp.lib = reinterpret_cast<const int32_t*>(base + ar.lib);
+  kp.order = reinterpret_cast<const int32_t*>(base + ar.order);
   kp.partials = reinterpret_cast<double*>(base + ar.part);
   kp.unit_done = reinterpret_cast<uint32_t*>(base + ar.done);
   kp.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter);
   kp.rho = reinterpret_cast<double*>(base + ar.rho);
   kp.err = reinterpret_cast<int32_t*>(base + ar.err);
   kp.persistent = persistent;
+  for (int e = 0; e <= kMaxE; ++e) kp.merge_at[e] = kDefaultMergeAt;
+  if (const char* env = getenv("CCM_MERGE_AT"))
+    for (int e = 0; e <= kMaxE; ++e) kp.merge_at[e] = atoi(env);
   return kp;
 }
 
@@ -323,6 +352,10 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int gr
   sp.dbg_lib = dbg_lib;
   sp.dbg_lib_off = d_dbg_lib_off;
   if (ev) CCM_CUDA(record(ev[0]));
+  CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
+                        reinterpret_cast<const OrderJob*>(base + ar.orders),
+                        (int64_t)ul.orders.size(), ul.max_nm,
+                        reinterpret_cast<int32_t*>(base + ar.order), s));
   CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
   KnnParams kp = knn_params(base, ar, ul, persistent);
   kp.dbg_nbr = dbg_nbr;
@@ -369,6 +402,7 @@ ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context**
   if (prop.major < 10) return fail(CCM_EINVAL, "needs a Blackwell (sm_10x) GPU");
   CCM_CUDA(sampler_prepare());
   CCM_CUDA(knn_prepare());
+  CCM_CUDA(order_prepare());
   size_t free_b = 0, total_b = 0;
   CCM_CUDA(cudaMemGetInfo(&free_b, &total_b));
   std::unique_ptr<ccm_context> ctx(new ccm_context());
@@ -406,6 +440,9 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_arena + pl->ar.items, pl->ul.items.data(),
                    sizeof(WorkItem) * pl->ul.items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_arena + pl->ar.orders, pl->ul.orders.data(),
+                   sizeof(OrderJob) * pl->ul.orders.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemset(pl->d_arena + pl->ar.done, 0, sizeof(uint32_t) * pl->ul.units.size());
   if (e != cudaSuccess) {
@@ -638,6 +675,9 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
                            sizeof(UnitDesc) * b->ul.units.size(), cudaMemcpyHostToDevice, b->stream));
   CCM_CUDA(cudaMemcpyAsync(base + b->ar.items, b->ul.items.data(),
                            sizeof(WorkItem) * b->ul.items.size(), cudaMemcpyHostToDevice, b->stream));
+  CCM_CUDA(cudaMemcpyAsync(base + b->ar.orders, b->ul.orders.data(),
+                           sizeof(OrderJob) * b->ul.orders.size(), cudaMemcpyHostToDevice,
+                           b->stream));
   CCM_CUDA(cudaMemsetAsync(base + b->ar.done, 0, sizeof(uint32_t) * b->ul.units.size(), b->stream));
   ccm_status st = enqueue_sweep(base, b->ar, b->ul, 0, 0, nullptr, nullptr, nullptr, nullptr,
                                 b->stream);
