@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample-units", type=int, default=96)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=40)
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run every sweep cell with R realizations through ccm_run "
                          "twice (the small case for ncu captures) and exit")
@@ -295,9 +297,63 @@ def run_ours(args, rank, world, local_rank):
         }
         if not args.no_plain:
             out["vs_plain_gpu"] = compare_plain(ccm, ctx, I, p, torch)
+        if not args.no_serving:
+            out["serving"] = serve_stream(ccm, I, args.serving_jobs, local_rank)
     ccm.ccm_plan_destroy(plan)
     ccm.ccm_context_destroy(ctx)
     return out
+
+
+def serve_stream(ccm, I, n_jobs: int, device: int):
+    """Served request stream: the first n_jobs of the seeded job stream (lengths
+    log-uniform 500..50000, E 1..10, tau 1..5, r in {100, 250}).  Capacity is
+    calibrated by submitting every job at once; the stream is then replayed
+    with Poisson arrivals at 0.7 x that capacity, and per-job latency (submit to
+    finish, on the library's clock) is reported."""
+    import numpy as np
+    jobs = I.job_stream(n_jobs=n_jobs, rate_per_s=1.0)
+    ctx = ccm.ccm_context_create(device)
+
+    def run(arrivals):
+        t0 = time.perf_counter()
+        tickets = []
+        for a, j in zip(arrivals, jobs):
+            delay = a - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            q = j.problem
+            tickets.append(ccm.ccm_submit(ctx, q.series, q.pairs, q.E, q.tau, q.L, q.r, q.seed))
+        lat, first, last = [], None, None
+        for t, j in zip(tickets, jobs):
+            while True:
+                st, sub, start, fin = ccm.ccm_job_times(ctx, t)
+                if st == ccm.CCM_OK:
+                    break
+                time.sleep(0.001)
+            rho = np.zeros(ccm.rho_shape(j.problem))
+            ccm.ccm_poll(ctx, t, rho, 0)
+            lat.append(fin - sub)
+            first = sub if first is None else min(first, sub)
+            last = fin if last is None else max(last, fin)
+        return np.array(lat), last - first
+
+    try:
+        _, span = run([0.0] * n_jobs)                  # calibration: all at once
+        capacity = n_jobs / span
+        rate = 0.7 * capacity
+        arrivals = [j.arrival_s / rate for j in jobs]  # unit-rate Poisson times rescaled
+        lat, span2 = run(arrivals)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+    units = sum(j.problem.n_units() for j in jobs)
+    pairs = sum(j.problem.pair_count() for j in jobs)
+    return {"jobs": n_jobs, "stream": "first jobs of the seeded served stream (seed 20190505)",
+            "capacity_jobs_per_s": capacity, "arrival_rate_per_s": rate,
+            "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_latency_ms": float(lat.max() * 1e3),
+            "realizations_per_s": units / span2, "pairs": float(pairs),
+            "makespan_s": span2}
 
 
 def compare_plain(ccm, ctx, I, p, torch):

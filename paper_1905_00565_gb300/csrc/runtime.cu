@@ -263,12 +263,47 @@ struct ccm_context {
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   std::deque<std::shared_ptr<Job>> queue;
   std::list<std::shared_ptr<Batch>> inflight;
-  std::vector<cudaStream_t> streams;
-  size_t next_stream = 0;
-  int max_inflight = 4;
+  std::vector<cudaStream_t> streams;       // low priority: batches of large jobs
+  std::vector<cudaStream_t> fast_streams;  // high priority: batches of small jobs
+  size_t next_stream = 0, next_fast = 0;
+  int max_inflight = 8;
+  double batch_pairs = 5.0e10;             // query-library pairs per batch of small jobs
+  // Pinned staging buffers are pooled: cudaMallocHost/cudaFreeHost may
+  // synchronise the device, which would stall polls and new batches behind a
+  // running large job.  Size classes are powers of two.
+  std::mutex pool_mu;
+  std::multimap<size_t, void*> pool_free;
+  std::vector<void*> pool_all;
 };
 
 namespace {
+
+size_t pool_class(size_t bytes) {
+  size_t c = 256;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+
+void* pinned_get(ccm_context* ctx, size_t bytes) {
+  const size_t c = pool_class(bytes);
+  std::lock_guard<std::mutex> g(ctx->pool_mu);
+  auto it = ctx->pool_free.find(c);
+  if (it != ctx->pool_free.end()) {
+    void* ptr = it->second;
+    ctx->pool_free.erase(it);
+    return ptr;
+  }
+  void* ptr = nullptr;
+  if (cudaMallocHost(&ptr, c) != cudaSuccess) return nullptr;
+  ctx->pool_all.push_back(ptr);
+  return ptr;
+}
+
+void pinned_put(ccm_context* ctx, void* ptr, size_t bytes) {
+  if (!ptr) return;
+  std::lock_guard<std::mutex> g(ctx->pool_mu);
+  ctx->pool_free.emplace(pool_class(bytes), ptr);
+}
 
 ccm_status reserve(ccm_context* ctx, size_t bytes) {
   std::lock_guard<std::mutex> g(ctx->mu);
@@ -613,10 +648,12 @@ ccm_status ccm_run_plain(ccm_plan_t* plan, const float* series, double* rho, voi
 struct Job {
   uint64_t ticket = 0;
   ProblemCopy pc;
-  float* h_series = nullptr;  // pinned copy
-  double* h_rho = nullptr;    // pinned result
+  float* h_series = nullptr;  // pinned copy (from the context's pool)
+  double* h_rho = nullptr;    // pinned result (from the context's pool)
+  size_t series_bytes = 0, rho_bytes = 0;
   int64_t n_units = 0;
   size_t footprint = 0;
+  double pairs = 0.0;  // query-library pairs: the job's cost
   enum State { kQueued, kRunning, kDone, kFailed, kCancelled } state = kQueued;
   ccm_status status = CCM_PENDING;
   std::string err;
@@ -630,15 +667,18 @@ struct Batch {
   Arena ar;
   char* d_arena = nullptr;
   int32_t* h_err = nullptr;
+  void* h_meta = nullptr;  // pinned copy of units, items and order jobs for the async upload
+  size_t meta_bytes = 0;
   cudaStream_t stream = nullptr;
   std::atomic<bool> finished{false};
 };
 
 namespace {
 
-size_t job_footprint(const ProblemCopy& pc) {
+size_t job_footprint(const ProblemCopy& pc, double* pairs) {
   UnitList ul;
   append_units(pc, 0, 0, &ul);
+  *pairs = ul.pairs;
   return layout((int64_t)pc.V * pc.n, ul, (int64_t)ul.units.size(), 0).total;
 }
 
@@ -671,12 +711,21 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
                              cudaMemcpyHostToDevice, b->stream));
     so += (int64_t)j->pc.V * j->pc.n;
   }
-  CCM_CUDA(cudaMemcpyAsync(base + b->ar.units, b->ul.units.data(),
-                           sizeof(UnitDesc) * b->ul.units.size(), cudaMemcpyHostToDevice, b->stream));
-  CCM_CUDA(cudaMemcpyAsync(base + b->ar.items, b->ul.items.data(),
-                           sizeof(WorkItem) * b->ul.items.size(), cudaMemcpyHostToDevice, b->stream));
-  CCM_CUDA(cudaMemcpyAsync(base + b->ar.orders, b->ul.orders.data(),
-                           sizeof(OrderJob) * b->ul.orders.size(), cudaMemcpyHostToDevice,
+  // Descriptors go through pinned staging: a copy from pageable memory would
+  // wait for earlier work on this (reused) stream.
+  const size_t ub = sizeof(UnitDesc) * b->ul.units.size();
+  const size_t ib = sizeof(WorkItem) * b->ul.items.size();
+  const size_t ob = sizeof(OrderJob) * b->ul.orders.size();
+  b->meta_bytes = ub + ib + ob;
+  b->h_meta = pinned_get(ctx, b->meta_bytes);
+  if (!b->h_meta) return fail(CCM_ENOMEM, "pinned allocation failed");
+  char* hm = static_cast<char*>(b->h_meta);
+  std::memcpy(hm, b->ul.units.data(), ub);
+  std::memcpy(hm + ub, b->ul.items.data(), ib);
+  std::memcpy(hm + ub + ib, b->ul.orders.data(), ob);
+  CCM_CUDA(cudaMemcpyAsync(base + b->ar.units, hm, ub, cudaMemcpyHostToDevice, b->stream));
+  CCM_CUDA(cudaMemcpyAsync(base + b->ar.items, hm + ub, ib, cudaMemcpyHostToDevice, b->stream));
+  CCM_CUDA(cudaMemcpyAsync(base + b->ar.orders, hm + ub + ib, ob, cudaMemcpyHostToDevice,
                            b->stream));
   CCM_CUDA(cudaMemsetAsync(base + b->ar.done, 0, sizeof(uint32_t) * b->ul.units.size(), b->stream));
   ccm_status st = enqueue_sweep(base, b->ar, b->ul, 0, 0, nullptr, nullptr, nullptr, nullptr,
@@ -695,8 +744,13 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
   return CCM_OK;
 }
 
+// No CUDA call that may synchronise (cudaFreeHost, cudaMallocHost,
+// cudaStreamSynchronize, ...) is made while ctx->mu is held: the host callback
+// that marks a batch finished takes ctx->mu, and its stream cannot advance
+// until it returns.
 void serve(ccm_context* ctx) {
   cudaSetDevice(ctx->device);
+  std::vector<int32_t*> to_free;
   std::unique_lock<std::mutex> lk(ctx->mu);
   for (;;) {
     // Retire finished batches.
@@ -721,9 +775,19 @@ void serve(ccm_context* ctx) {
         }
       }
       ctx->used -= std::min(ctx->used, bytes);
-      cudaFreeHost(b->h_err);
+      // cudaFreeHost may synchronise; a pending host callback of another batch
+      // needs ctx->mu to finish, so free after releasing the lock.
+      to_free.push_back(b->h_err);
+      pinned_put(ctx, b->h_meta, b->meta_bytes);  // pool mutex only, no CUDA call
       it = ctx->inflight.erase(it);
       ctx->cv.notify_all();
+    }
+    if (!to_free.empty()) {
+      lk.unlock();
+      for (int32_t* ptr : to_free) pinned_put(ctx, ptr, sizeof(int32_t));
+      to_free.clear();
+      lk.lock();
+      continue;  // state may have changed while unlocked
     }
     if (ctx->stop && ctx->inflight.empty()) break;
     // Admit queued jobs into a new batch while their footprints fit.
@@ -732,6 +796,9 @@ void serve(ccm_context* ctx) {
       b->ctx = ctx;
       size_t bytes = 0;
       int64_t units = 0;
+      double pairs = 0.0;
+      // A batch takes queued jobs in order while they fit the free budget; a
+      // large job runs alone, small ones are grouped up to batch_pairs.
       while (!ctx->queue.empty()) {
         auto& j = ctx->queue.front();
         if (j->state == Job::kCancelled) {
@@ -739,9 +806,12 @@ void serve(ccm_context* ctx) {
           continue;
         }
         if (ctx->used + bytes + j->footprint > ctx->budget) break;
-        if (!b->jobs.empty() && units + j->n_units > (int64_t)1 << 22) break;
+        if (!b->jobs.empty() && (units + j->n_units > (int64_t)1 << 22 ||
+                                 pairs + j->pairs > ctx->batch_pairs))
+          break;
         bytes += j->footprint;
         units += j->n_units;
+        pairs += j->pairs;
         b->jobs.push_back(j);
         ctx->queue.pop_front();
       }
@@ -752,12 +822,14 @@ void serve(ccm_context* ctx) {
           j->state = Job::kRunning;
           j->t_start = t;
         }
-        b->stream = ctx->streams[ctx->next_stream++ % ctx->streams.size()];
+        b->stream = (pairs <= ctx->batch_pairs)
+                        ? ctx->fast_streams[ctx->next_fast++ % ctx->fast_streams.size()]
+                        : ctx->streams[ctx->next_stream++ % ctx->streams.size()];
         ctx->inflight.push_back(b);
         lk.unlock();
-        cudaError_t he = cudaMallocHost(&b->h_err, sizeof(int32_t));
-        ccm_status st = (he == cudaSuccess) ? launch_batch(ctx, b.get())
-                                            : fail(CCM_ENOMEM, "pinned allocation failed");
+        b->h_err = static_cast<int32_t*>(pinned_get(ctx, sizeof(int32_t)));
+        ccm_status st = b->h_err ? launch_batch(ctx, b.get())
+                                 : fail(CCM_ENOMEM, "pinned allocation failed");
         lk.lock();
         if (st != CCM_OK) {
           // Nothing more will run for this batch once the stream drains.
@@ -772,7 +844,8 @@ void serve(ccm_context* ctx) {
             j->t_finish = now_s();
           }
           ctx->used -= std::min(ctx->used, bytes);
-          if (b->h_err) cudaFreeHost(b->h_err);
+          if (b->h_err) to_free.push_back(b->h_err);
+          pinned_put(ctx, b->h_meta, b->meta_bytes);
           ctx->inflight.remove(b);
           ctx->cv.notify_all();
         }
@@ -786,21 +859,23 @@ void serve(ccm_context* ctx) {
 ccm_status ensure_server(ccm_context* ctx) {
   std::lock_guard<std::mutex> g(ctx->mu);
   if (ctx->server_started) return CCM_OK;
-  int lo = 0, hi = 0;
-  CCM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-  for (int q = 0; q < ctx->max_inflight; ++q) {
+  int least = 0, greatest = 0;
+  CCM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  for (int q = 0; q < ctx->max_inflight / 2; ++q) {
     cudaStream_t s;
-    CCM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    CCM_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least));
     ctx->streams.push_back(s);
+    CCM_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
+    ctx->fast_streams.push_back(s);
   }
   ctx->server = std::thread(serve, ctx);
   ctx->server_started = true;
   return CCM_OK;
 }
 
-void free_job(Job* j) {
-  if (j->h_series) cudaFreeHost(j->h_series);
-  if (j->h_rho) cudaFreeHost(j->h_rho);
+void free_job(ccm_context* ctx, Job* j) {
+  pinned_put(ctx, j->h_series, j->series_bytes);
+  pinned_put(ctx, j->h_rho, j->rho_bytes);
   j->h_series = nullptr;
   j->h_rho = nullptr;
 }
@@ -820,17 +895,19 @@ ccm_status ccm_submit(ccm_context* ctx, const ccm_problem* prob, const float* se
   const size_t elems = (size_t)j->pc.V * (size_t)j->pc.n;
   if (!all_finite(series, elems)) return fail(CCM_EINVAL, "series holds a non-finite value");
   j->n_units = j->pc.n_units();
-  j->footprint = job_footprint(j->pc);
+  j->footprint = job_footprint(j->pc, &j->pairs);
   if (j->footprint > ctx->budget)
     return fail(CCM_ETOOLARGE, "job footprint " + std::to_string(j->footprint) +
                                    " B exceeds the context budget");
   CCM_CUDA(cudaSetDevice(ctx->device));
   st = ensure_server(ctx);
   if (st != CCM_OK) return st;
-  CCM_CUDA(cudaMallocHost(&j->h_series, sizeof(float) * elems));
-  cudaError_t e = cudaMallocHost(&j->h_rho, sizeof(double) * (size_t)j->n_units);
-  if (e != cudaSuccess) {
-    free_job(j.get());
+  j->series_bytes = sizeof(float) * elems;
+  j->rho_bytes = sizeof(double) * (size_t)j->n_units;
+  j->h_series = static_cast<float*>(pinned_get(ctx, j->series_bytes));
+  j->h_rho = static_cast<double*>(pinned_get(ctx, j->rho_bytes));
+  if (!j->h_series || !j->h_rho) {
+    free_job(ctx, j.get());
     return fail(CCM_ENOMEM, "pinned allocation failed");
   }
   std::memcpy(j->h_series, series, sizeof(float) * elems);
@@ -867,7 +944,7 @@ ccm_status ccm_poll(ccm_context* ctx, uint64_t ticket, double* rho, int32_t time
   }
   ctx->jobs.erase(it);
   lk.unlock();
-  free_job(j.get());
+  free_job(ctx, j.get());
   return st;
 }
 
@@ -918,8 +995,10 @@ ccm_status ccm_context_destroy(ccm_context* ctx) {
   if (ctx->server_started) ctx->server.join();
   cudaSetDevice(ctx->device);
   for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
-  for (auto& kv : ctx->jobs) free_job(kv.second.get());
+  for (cudaStream_t s : ctx->fast_streams) cudaStreamDestroy(s);
+  for (auto& kv : ctx->jobs) free_job(ctx, kv.second.get());
   ctx->jobs.clear();
+  for (void* ptr : ctx->pool_all) cudaFreeHost(ptr);
   delete ctx;
   return CCM_OK;
 }
