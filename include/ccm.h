@@ -180,7 +180,7 @@ ccm_status ccm_job_times(ccm_context* ctx, uint64_t ticket, double* submit_s, do
  * d_series: device [n_series][n] FP32 (not checked for non-finite values);
  * d_rho: device [r] FP64, written in stream order.  All scratch lives in one
  * fixed 16 MiB device array held by every GPU that loads the library until
- * exit; a cell needing more (about r*L*4 + r*ceil(N_m/512)*56 + r*100 +
+ * exit; a cell needing more (about r*L*4 + r*ceil(N_m/256)*56 + r*150 +
  * N_m*4 bytes)
  * returns CCM_ETOOLARGE with a message and runs nothing.  Nothing is
  * allocated.  The first call on a device (with that device current) finds

@@ -9,22 +9,34 @@ namespace ccm {
 
 constexpr int kMaxE = 10;
 
-// One realization ("unit"): pair (j, i), E, tau, L, realization k of one job.
+// One library realization ("unit"): library variable j, E, tau, L, realization
+// k of one job, with the targets it is cross-mapped to.  The library and the
+// neighbour lists do not depend on the target, so all pairs (j, i) of a job
+// that share j are computed from one neighbour search.
 struct UnitDesc {
   int64_t series_off;   // element offset of the job's series block [V][n]
   int64_t n;            // series length of the job
   int64_t lib_off;      // offset of this unit's library in the library buffer
-  int64_t part_off;     // first partial-moment slot (one per query tile)
-  int64_t q_off;        // first query of this unit in the concatenated debug outputs
-  int64_t nbr_off;      // first neighbour entry in the concatenated debug outputs
-  int64_t out_idx;      // index of this unit's rho in the rho buffer
+  int64_t part_off;     // first partial-moment slot: target t, tile q at part_off + t*n_tiles + q
   int64_t order_off;    // first entry of this unit's query order (per variable, E, tau)
+  int64_t tgt_off;      // first TargetDesc of this unit
   uint64_t seed;        // library sampler seed of the job
-  int32_t j, i;         // library variable, target variable
+  int32_t j;            // library variable
   int32_t E, tau;
   int32_t L, k;
   int32_t n_m;          // manifold points = queries
   int32_t n_tiles;      // query tiles of the fused kernel
+  int32_t n_targets;    // targets cross-mapped from this library (>= 1)
+};
+
+// One target of a unit: the pair (j, i) and where its outputs go.
+struct TargetDesc {
+  int64_t out_idx;      // index of this (pair, E, tau, L, k) in the rho buffer
+  int64_t q_off;        // first query of this pair-realization in the debug predictions
+  int64_t nbr_off;      // first entry in the debug neighbour lists
+  int64_t lib_dbg_off;  // first entry in the debug libraries
+  int32_t i;            // target variable
+  int32_t pad;
 };
 
 // One work item of the fused kernel: a query tile of a unit.
@@ -45,9 +57,9 @@ constexpr int kOrderMaxSort = 16384;   // manifolds up to this size are sorted
 // Sampler: one CTA per unit.
 struct SamplerParams {
   const UnitDesc* units;
+  const TargetDesc* targets;  // for the debug copies (lib_dbg_off per target)
   int32_t* lib;           // library buffer (sum of L)
-  int32_t* dbg_lib;       // optional: libraries again, concatenated in unit order
-  const int64_t* dbg_lib_off;  // per-unit offsets into dbg_lib (NULL when dbg_lib is NULL)
+  int32_t* dbg_lib;       // optional: libraries again, once per target, in rho order
   int32_t* err;           // error flag (set, never cleared, by the kernels)
 };
 
@@ -55,6 +67,7 @@ struct SamplerParams {
 struct KnnParams {
   const float* series;    // device series blocks
   const UnitDesc* units;
+  const TargetDesc* targets;
   const WorkItem* items;
   int64_t n_items;
   const int32_t* lib;
@@ -102,7 +115,7 @@ void set_last_error(const char* msg);
 
 // Plain comparator (plain.cu): one realization per call.
 cudaError_t launch_plain_unit(const float* series, const UnitDesc* unit_dev, const UnitDesc& unit,
-                              const int32_t* lib, float* xhat_scratch, double* rho_out,
-                              int32_t* dbg_nbr, float* dbg_xhat, int32_t* err, cudaStream_t s);
+                              const TargetDesc* target_dev, const int32_t* lib,
+                              float* xhat_scratch, double* rho_out, cudaStream_t s);
 
 }  // namespace ccm

@@ -209,7 +209,6 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   const int n_m = u.n_m, L = u.L, tau = u.tau;
   const int off = (E - 1) * tau;
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
-  const float* si = p.series + u.series_off + (int64_t)u.i * u.n;
   const int32_t* lib = p.lib + u.lib_off;
   const int32_t* order = p.order + u.order_off;
   constexpr int kStep = kStepE<E>;
@@ -315,59 +314,76 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
     dd[s] = (s < self) ? kd[s] : kd[s + 1];
     nb[s] = (s < self) ? kl[s] : kl[s + 1];
   }
+  // Simplex weights (Sect. 2.1), once per query for every target.
   const float d1 = sqrtf(dd[0]);
-  float usum = 0.f, acc = 0.f;
+  float w[E + 1];
+  int nbc[E + 1];
+  float usum = 0.f;
 #pragma unroll
   for (int s = 0; s <= E; ++s) {
     const float di = sqrtf(dd[s]);
-    const float ui = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
-    usum += ui;
+    w[s] = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
+    usum += w[s];
     // an unfilled slot (only possible with non-finite device input) reads in bounds
-    const int nbc = min(max(nb[s], 0), n_m - 1);
-    acc = fmaf(ui, si[nbc + off], acc);
+    nbc[s] = min(max(nb[s], 0), n_m - 1);
   }
-  const float xhat = acc / usum;
-  const double xo = valid ? (double)si[m + off] : 0.0;
-  const double xp = valid ? (double)xhat : 0.0;
-  if (valid) {
-    if (p.dbg_xhat) p.dbg_xhat[u.q_off + m] = xhat;
-    if (p.dbg_nbr) {
+
+  for (int t = 0; t < u.n_targets; ++t) {
+    const TargetDesc tg = p.targets[u.tgt_off + t];
+    const float* si = p.series + u.series_off + (int64_t)tg.i * u.n;
+    float acc = 0.f;
 #pragma unroll
-      for (int s = 0; s <= E; ++s) p.dbg_nbr[u.nbr_off + (int64_t)m * (E + 1) + s] = nb[s];
+    for (int s = 0; s <= E; ++s) acc = fmaf(w[s], si[nbc[s] + off], acc);
+    const float xhat = acc / usum;
+    const double xo = valid ? (double)si[m + off] : 0.0;
+    const double xp = valid ? (double)xhat : 0.0;
+    if (valid) {
+      if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
+      if (p.dbg_nbr) {
+#pragma unroll
+        for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nb[s];
+      }
+    }
+    // Tile moments of this target, two passes over the registers.
+    double n = valid ? 1.0 : 0.0, sx = xo, sy = xp;
+    block_sum3(n, sx, sy, s_red);
+    const double mx = sx / n, my = sy / n;
+    double sxx = 0.0, syy = 0.0, sxy = 0.0;
+    if (valid) {
+      const double a = xo - mx, b = xp - my;
+      sxx = a * a;
+      syy = b * b;
+      sxy = a * b;
+    }
+    block_sum3(sxx, syy, sxy, s_red);
+    if (tid == 0) {
+      double* part = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile);
+      part[0] = n;
+      part[1] = mx;
+      part[2] = my;
+      part[3] = sxx;
+      part[4] = syy;
+      part[5] = sxy;
     }
   }
 
-  // Tile moments, two passes over the registers.
-  double n = valid ? 1.0 : 0.0, sx = xo, sy = xp;
-  block_sum3(n, sx, sy, s_red);
-  const double mx = sx / n, my = sy / n;
-  double sxx = 0.0, syy = 0.0, sxy = 0.0;
-  if (valid) {
-    const double a = xo - mx, b = xp - my;
-    sxx = a * a;
-    syy = b * b;
-    sxy = a * b;
-  }
-  block_sum3(sxx, syy, sxy, s_red);
-
+  // The last tile of this realization to finish merges every target's tile
+  // moments in tile order (Chan et al. pairwise update): rho does not depend
+  // on which CTA ran which tile, or when.
   if (tid == 0) {
-    double* part = p.partials + 6 * (u.part_off + tile);
-    part[0] = n;
-    part[1] = mx;
-    part[2] = my;
-    part[3] = sxx;
-    part[4] = syy;
-    part[5] = sxy;
     __threadfence();
     const unsigned prev = atomicAdd(&p.unit_done[unit], 1u);
     *s_last = (prev == (unsigned)(u.n_tiles - 1)) ? 1 : 0;
-    if (*s_last) {
-      __threadfence();
-      const double* base = p.partials + 6 * u.part_off;
+  }
+  __syncthreads();
+  if (*s_last) {
+    __threadfence();
+    for (int t = tid; t < u.n_targets; t += kThreads) {
+      const double* base = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles);
       double N = __ldcg(base + 0), MX = __ldcg(base + 1), MY = __ldcg(base + 2);
       double SXX = __ldcg(base + 3), SYY = __ldcg(base + 4), SXY = __ldcg(base + 5);
-      for (int t = 1; t < u.n_tiles; ++t) {
-        const double* pt = base + 6 * t;
+      for (int q = 1; q < u.n_tiles; ++q) {
+        const double* pt = base + 6 * q;
         const double nb2 = __ldcg(pt + 0), mxb = __ldcg(pt + 1), myb = __ldcg(pt + 2);
         const double tot = N + nb2;
         const double dx = mxb - MX, dy = myb - MY;
@@ -379,9 +395,10 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
         MY += dy * nb2 / tot;
         N = tot;
       }
-      p.rho[u.out_idx] = (SXX > 0.0 && SYY > 0.0) ? SXY / sqrt(SXX * SYY) : nan("");
-      p.unit_done[unit] = 0u;  // ready for the next run
+      p.rho[p.targets[u.tgt_off + t].out_idx] =
+          (SXX > 0.0 && SYY > 0.0) ? SXY / sqrt(SXX * SYY) : nan("");
     }
+    if (tid == 0) p.unit_done[unit] = 0u;  // ready for the next run
   }
   __syncthreads();
 }

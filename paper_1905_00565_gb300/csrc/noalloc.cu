@@ -37,7 +37,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 namespace {
 
 struct NoallocLayout {
-  size_t units, items, lib, part, done, err, counter, order, orderjob, total;
+  size_t units, items, lib, part, done, err, counter, order, orderjob, target, total;
 };
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
@@ -63,6 +63,8 @@ NoallocLayout noalloc_layout(int64_t r, int64_t L, int64_t n_tiles, int64_t n_m)
   o = up256(o + sizeof(int32_t) * (size_t)n_m);
   a.orderjob = o;
   o = up256(o + sizeof(OrderJob));
+  a.target = o;
+  o = up256(o + sizeof(TargetDesc) * (size_t)r);
   a.total = o;
   return a;
 }
@@ -92,19 +94,25 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     u.n = c.n;
     u.lib_off = k * (int64_t)c.L;
     u.part_off = k * (int64_t)c.n_tiles;
-    u.q_off = k * (int64_t)c.n_m;
-    u.nbr_off = k * (int64_t)c.n_m * (c.E + 1);
-    u.out_idx = k;
     u.order_off = 0;
+    u.tgt_off = k;
     u.seed = c.seed;
     u.j = c.j;
-    u.i = c.i;
     u.E = c.E;
     u.tau = c.tau;
     u.L = c.L;
     u.k = (int32_t)k;
     u.n_m = c.n_m;
     u.n_tiles = c.n_tiles;
+    u.n_targets = 1;
+    TargetDesc tg;
+    tg.out_idx = k;
+    tg.q_off = k * (int64_t)c.n_m;
+    tg.nbr_off = k * (int64_t)c.n_m * (c.E + 1);
+    tg.lib_dbg_off = k * (int64_t)c.L;
+    tg.i = c.i;
+    tg.pad = 0;
+    reinterpret_cast<TargetDesc*>(scratch + lay.target)[k] = tg;
     units[k] = u;
     done[k] = 0u;
   }
@@ -193,6 +201,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   if (e != cudaSuccess) return noalloc_fail(CCM_ECUDA, cudaGetErrorString(e));
   SamplerParams sp{};
   sp.units = reinterpret_cast<const UnitDesc*>(scratch + lay.units);
+  sp.targets = reinterpret_cast<const TargetDesc*>(scratch + lay.target);
   sp.lib = reinterpret_cast<int32_t*>(scratch + lay.lib);
   sp.err = reinterpret_cast<int32_t*>(scratch + lay.err);
   e = launch_sampler(sp, 0, r, (int)n_m, s);
@@ -200,6 +209,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   KnnParams kp{};
   kp.series = d_series;
   kp.units = reinterpret_cast<const UnitDesc*>(scratch + lay.units);
+  kp.targets = reinterpret_cast<const TargetDesc*>(scratch + lay.target);
   kp.items = reinterpret_cast<const WorkItem*>(scratch + lay.items);
   kp.n_items = (int64_t)r * n_tiles;
   kp.lib = reinterpret_cast<const int32_t*>(scratch + lay.lib);

@@ -1,9 +1,9 @@
 // Plain GPU CCM: the straightforward CUDA form of one realization, kept as
-// the comparator the batched path is measured against.  Per realization it
-// launches the sampler for one unit, a naive kNN kernel (one thread per
-// query, library coordinates gathered from global memory for every query,
-// a sorted insertion into a local top-(E+2) list) that writes the
-// predictions, and a one-CTA FP64 Pearson kernel.  Same selection rule and
+// the comparator the batched path is measured against.  Per realization
+// (pair, E, tau, L, k) it launches the sampler, a naive kNN kernel (one
+// thread per query, library coordinates gathered from global memory for
+// every query, a sorted insertion into a local top-(E+2) list) that writes
+// the predictions, and a one-CTA FP64 Pearson kernel.  Same selection rule and
 // rounding sequence as the fused kernel, hence the same neighbours.
 #include <math.h>
 
@@ -16,14 +16,15 @@ constexpr int kPlainThreads = 128;
 constexpr int kRhoThreads = 1024;
 
 __global__ void __launch_bounds__(kPlainThreads)
-plain_knn_kernel(const float* series, const UnitDesc* unit, const int32_t* lib, float* xhat,
-                 int32_t* dbg_nbr, float* dbg_xhat) {
+plain_knn_kernel(const float* series, const UnitDesc* unit, const TargetDesc* target,
+                 const int32_t* lib, float* xhat) {
   const UnitDesc u = *unit;
+  const TargetDesc tg = *target;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= u.n_m) return;
   const int E = u.E, tau = u.tau, off = (E - 1) * tau, K = E + 2;
   const float* sj = series + u.series_off + (int64_t)u.j * u.n;
-  const float* si = series + u.series_off + (int64_t)u.i * u.n;
+  const float* si = series + u.series_off + (int64_t)tg.i * u.n;
   const int32_t* ul = lib + u.lib_off;
   float q[kMaxE];
   for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
@@ -72,19 +73,17 @@ plain_knn_kernel(const float* series, const UnitDesc* unit, const int32_t* lib, 
     const int nbc = min(max(kl[s], 0), u.n_m - 1);  // in bounds even for non-finite input
     accx = fmaf(ui, si[nbc + off], accx);
   }
-  const float xh = accx / usum;
-  xhat[m] = xh;
-  if (dbg_xhat) dbg_xhat[u.q_off + m] = xh;
-  if (dbg_nbr)
-    for (int s = 0; s <= E; ++s) dbg_nbr[u.nbr_off + (int64_t)m * (E + 1) + s] = kl[s];
+  xhat[m] = accx / usum;
 }
 
 __global__ void __launch_bounds__(kRhoThreads)
-plain_rho_kernel(const float* series, const UnitDesc* unit, const float* xhat, double* rho) {
+plain_rho_kernel(const float* series, const UnitDesc* unit, const TargetDesc* target,
+                 const float* xhat, double* rho) {
   __shared__ double s_a[kRhoThreads], s_b[kRhoThreads], s_c[kRhoThreads];
   const UnitDesc u = *unit;
+  const TargetDesc tg = *target;
   const int off = (u.E - 1) * u.tau;
-  const float* si = series + u.series_off + (int64_t)u.i * u.n;
+  const float* si = series + u.series_off + (int64_t)tg.i * u.n;
   double a = 0.0, b = 0.0;
   for (int m = threadIdx.x; m < u.n_m; m += blockDim.x) {
     a += (double)si[m + off];
@@ -122,18 +121,17 @@ plain_rho_kernel(const float* series, const UnitDesc* unit, const float* xhat, d
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    rho[u.out_idx] = (s_a[0] > 0.0 && s_b[0] > 0.0) ? s_c[0] / sqrt(s_a[0] * s_b[0]) : nan("");
+    rho[tg.out_idx] = (s_a[0] > 0.0 && s_b[0] > 0.0) ? s_c[0] / sqrt(s_a[0] * s_b[0]) : nan("");
 }
 
 }  // namespace
 
 cudaError_t launch_plain_unit(const float* series, const UnitDesc* unit_dev, const UnitDesc& unit,
-                              const int32_t* lib, float* xhat_scratch, double* rho_out,
-                              int32_t* dbg_nbr, float* dbg_xhat, int32_t*, cudaStream_t s) {
+                              const TargetDesc* target_dev, const int32_t* lib,
+                              float* xhat_scratch, double* rho_out, cudaStream_t s) {
   const unsigned grid = (unsigned)((unit.n_m + kPlainThreads - 1) / kPlainThreads);
-  plain_knn_kernel<<<grid, kPlainThreads, 0, s>>>(series, unit_dev, lib, xhat_scratch, dbg_nbr,
-                                                  dbg_xhat);
-  plain_rho_kernel<<<1, kRhoThreads, 0, s>>>(series, unit_dev, xhat_scratch, rho_out);
+  plain_knn_kernel<<<grid, kPlainThreads, 0, s>>>(series, unit_dev, target_dev, lib, xhat_scratch);
+  plain_rho_kernel<<<1, kRhoThreads, 0, s>>>(series, unit_dev, target_dev, xhat_scratch, rho_out);
   return cudaGetLastError();
 }
 

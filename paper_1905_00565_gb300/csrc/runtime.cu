@@ -119,50 +119,82 @@ bool all_finite(const float* x, size_t count) {
 
 // ------------------------------------------------------------- unit lists ---
 struct UnitList {
-  std::vector<UnitDesc> units;
+  std::vector<UnitDesc> units;        // library realizations
+  std::vector<TargetDesc> targets;    // their targets (one per output rho)
   std::vector<WorkItem> items;
   std::vector<double> item_cost;
-  std::vector<OrderJob> orders;  // one per (job, library variable, E, tau)
-  int64_t lib_total = 0, part_total = 0, q_total = 0, nbr_total = 0, order_total = 0;
+  std::vector<OrderJob> orders;       // one per (job, library variable, E, tau)
+  int64_t lib_total = 0, part_total = 0, order_total = 0;
+  int64_t n_rho = 0, q_total = 0, nbr_total = 0, lib_dbg_total = 0;  // per output realization
   int emin = kMaxE + 1, emax = 0, max_nm = 0;
-  double pairs = 0.0, flops = 0.0;
+  double pairs = 0.0, flops = 0.0;    // neighbour-search work actually done
 };
 
 // Append the units of one problem.  Offsets: series block, first rho index.
+// Pairs that share a library variable j share one library and one neighbour
+// search per (E, tau, L, k); each pair becomes a target of that unit.
 void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, UnitList* ul) {
   const int tileq = knn_block_threads() * knn_queries_per_thread();
   const int64_t nP = (int64_t)pc.pairs.size() / 2;
-  int64_t out = out_base;
+  const int64_t nE = (int64_t)pc.E.size(), nT = (int64_t)pc.tau.size(), nL = (int64_t)pc.L.size();
+  const int64_t per_pair = nE * nT * nL * pc.r;
+  // debug offsets of every output realization, in rho order
+  std::vector<int64_t> q_off((size_t)(nP * per_pair)), nbr_off(q_off.size()), lib_off(q_off.size());
+  {
+    int64_t o = 0;
+    for (int64_t p = 0; p < nP; ++p)
+      for (int32_t E : pc.E)
+        for (int32_t tau : pc.tau)
+          for (int64_t L : pc.L)
+            for (int32_t k = 0; k < pc.r; ++k, ++o) {
+              const int64_t n_m = pc.n - (int64_t)(E - 1) * tau;
+              q_off[(size_t)o] = ul->q_total;
+              nbr_off[(size_t)o] = ul->nbr_total;
+              lib_off[(size_t)o] = ul->lib_dbg_total;
+              ul->q_total += n_m;
+              ul->nbr_total += n_m * (E + 1);
+              ul->lib_dbg_total += L;
+            }
+    ul->n_rho += o;
+  }
+  // library variables in order of first appearance, with their pairs
+  std::vector<int32_t> lib_vars;
+  std::map<int32_t, std::vector<int64_t>> pairs_of;
+  for (int64_t p = 0; p < nP; ++p) {
+    const int32_t j = pc.pairs[2 * p];
+    if (!pairs_of.count(j)) lib_vars.push_back(j);
+    pairs_of[j].push_back(p);
+  }
   std::map<std::tuple<int32_t, int32_t, int32_t>, int64_t> combo;  // (j, E, tau) -> order_off
-  for (int64_t p = 0; p < nP; ++p)
+  for (int32_t j : lib_vars)
     for (int32_t E : pc.E)
       for (int32_t tau : pc.tau) {
-        const auto key = std::make_tuple(pc.pairs[2 * p], E, tau);
-        if (combo.count(key)) continue;
         OrderJob oj;
         std::memset(&oj, 0, sizeof(oj));
         oj.series_off = series_off;
         oj.n = pc.n;
         oj.order_off = ul->order_total;
-        oj.j = pc.pairs[2 * p];
+        oj.j = j;
         oj.E = E;
         oj.tau = tau;
         oj.n_m = (int32_t)(pc.n - (int64_t)(E - 1) * tau);
-        combo[key] = oj.order_off;
+        combo[std::make_tuple(j, E, tau)] = oj.order_off;
         ul->order_total += oj.n_m;
         ul->orders.push_back(oj);
       }
-  for (int64_t p = 0; p < nP; ++p)
-    for (int32_t E : pc.E)
-      for (int32_t tau : pc.tau)
-        for (int64_t L : pc.L)
+  for (int32_t j : lib_vars) {
+    const std::vector<int64_t>& tp = pairs_of[j];
+    for (int64_t e = 0; e < nE; ++e)
+      for (int64_t t = 0; t < nT; ++t)
+        for (int64_t l = 0; l < nL; ++l)
           for (int32_t k = 0; k < pc.r; ++k) {
+            const int32_t E = pc.E[(size_t)e], tau = pc.tau[(size_t)t];
+            const int64_t L = pc.L[(size_t)l];
             UnitDesc u;
             std::memset(&u, 0, sizeof(u));
             u.series_off = series_off;
             u.n = pc.n;
-            u.j = pc.pairs[2 * p];
-            u.i = pc.pairs[2 * p + 1];
+            u.j = j;
             u.E = E;
             u.tau = tau;
             u.L = (int32_t)L;
@@ -170,23 +202,32 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
             u.seed = pc.seed;
             u.n_m = (int32_t)(pc.n - (int64_t)(E - 1) * tau);
             u.n_tiles = (u.n_m + tileq - 1) / tileq;
+            u.n_targets = (int32_t)tp.size();
             u.lib_off = ul->lib_total;
             u.part_off = ul->part_total;
-            u.q_off = ul->q_total;
-            u.nbr_off = ul->nbr_total;
-            u.out_idx = out++;
-            u.order_off = combo[std::make_tuple(u.j, E, tau)];
+            u.order_off = combo[std::make_tuple(j, E, tau)];
+            u.tgt_off = (int64_t)ul->targets.size();
+            for (int64_t p : tp) {
+              const int64_t o = (((p * nE + e) * nT + t) * nL + l) * pc.r + k;  // rho order
+              TargetDesc tg;
+              std::memset(&tg, 0, sizeof(tg));
+              tg.out_idx = out_base + o;
+              tg.q_off = q_off[(size_t)o];
+              tg.nbr_off = nbr_off[(size_t)o];
+              tg.lib_dbg_off = lib_off[(size_t)o];
+              tg.i = pc.pairs[2 * p + 1];
+              ul->targets.push_back(tg);
+            }
             const int32_t uidx = (int32_t)ul->units.size();
-            for (int32_t t = 0; t < u.n_tiles; ++t) {
-              const int64_t nq = std::min<int64_t>(tileq, u.n_m - (int64_t)t * tileq);
-              ul->items.push_back(WorkItem{uidx, t});
-              // distance work plus a fixed cost per library point for staging
-              ul->item_cost.push_back((double)L * ((double)nq * (2.0 * E + 1.0) + 64.0 * E));
+            for (int32_t q = 0; q < u.n_tiles; ++q) {
+              const int64_t nq = std::min<int64_t>(tileq, u.n_m - (int64_t)q * tileq);
+              ul->items.push_back(WorkItem{uidx, q});
+              // distance work, staging per library point, per-target epilogue
+              ul->item_cost.push_back((double)L * ((double)nq * (2.0 * E + 1.0) + 64.0 * E) +
+                                      (double)u.n_targets * nq * 64.0);
             }
             ul->lib_total += L;
-            ul->part_total += u.n_tiles;
-            ul->q_total += u.n_m;
-            ul->nbr_total += (int64_t)u.n_m * (E + 1);
+            ul->part_total += (int64_t)u.n_tiles * u.n_targets;
             ul->emin = std::min(ul->emin, E);
             ul->emax = std::max(ul->emax, E);
             ul->max_nm = std::max(ul->max_nm, u.n_m);
@@ -194,6 +235,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
             ul->flops += 3.0 * E * (double)u.n_m * (double)L;
             ul->units.push_back(u);
           }
+  }
 }
 
 // Sort the work list by decreasing cost (longest first), ties by position.
@@ -211,7 +253,7 @@ void sort_items(UnitList* ul) {
 // Device arena layout for a unit list.
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
-         counter = 0, scratch = 0, order = 0, orders = 0, total = 0;
+         counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, total = 0;
 };
 
 Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
@@ -234,6 +276,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.scratch = take(sizeof(float) * (size_t)scratch_floats);
   a.order = take(sizeof(int32_t) * (size_t)ul.order_total);
   a.orders = take(sizeof(OrderJob) * ul.orders.size());
+  a.targets = take(sizeof(TargetDesc) * ul.targets.size());
   a.total = o;
   return a;
 }
@@ -344,6 +387,7 @@ namespace {
 SamplerParams sampler_params(char* base, const Arena& ar) {
   SamplerParams sp{};
   sp.units = reinterpret_cast<const UnitDesc*>(base + ar.units);
+  sp.targets = reinterpret_cast<const TargetDesc*>(base + ar.targets);
   sp.lib = reinterpret_cast<int32_t*>(base + ar.lib);
   sp.err = reinterpret_cast<int32_t*>(base + ar.err);
   return sp;
@@ -353,6 +397,7 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   KnnParams kp{};
   kp.series = reinterpret_cast<const float*>(base + ar.series);
   kp.units = reinterpret_cast<const UnitDesc*>(base + ar.units);
+  kp.targets = reinterpret_cast<const TargetDesc*>(base + ar.targets);
   kp.items = reinterpret_cast<const WorkItem*>(base + ar.items);
   kp.n_items = (int64_t)ul.items.size();
   kp.lib = reinterpret_cast<const int32_t*>(base + ar.lib);
@@ -371,8 +416,8 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
 
 // Enqueue sampler + fused kernel for a whole unit list on stream s.
 ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int grid, int persistent,
-                         int32_t* dbg_lib, const int64_t* d_dbg_lib_off, int32_t* dbg_nbr,
-                         float* dbg_xhat, cudaStream_t s, cudaEvent_t* ev = nullptr,
+                         int32_t* dbg_lib, int32_t* dbg_nbr, float* dbg_xhat, cudaStream_t s,
+                         cudaEvent_t* ev = nullptr,
                          bool capturing = false) {
   // Inside stream capture an event record becomes a graph node only with the
   // external flag; outside capture the plain record is the valid form.
@@ -385,7 +430,6 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int gr
   CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
   SamplerParams sp = sampler_params(base, ar);
   sp.dbg_lib = dbg_lib;
-  sp.dbg_lib_off = d_dbg_lib_off;
   if (ev) CCM_CUDA(record(ev[0]));
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
                         reinterpret_cast<const OrderJob*>(base + ar.orders),
@@ -458,7 +502,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   append_units(pl->pc, 0, 0, &pl->ul);
   sort_items(&pl->ul);
   const int64_t series_elems = (int64_t)pl->pc.V * pl->pc.n;
-  pl->ar = layout(series_elems, pl->ul, (int64_t)pl->ul.units.size(), pl->ul.max_nm);
+  pl->ar = layout(series_elems, pl->ul, pl->ul.n_rho, pl->ul.max_nm);
   CCM_CUDA(cudaSetDevice(ctx->device));
   st = reserve(ctx, pl->ar.total);
   if (st != CCM_OK) return st;
@@ -479,6 +523,9 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
     e = cudaMemcpy(pl->d_arena + pl->ar.orders, pl->ul.orders.data(),
                    sizeof(OrderJob) * pl->ul.orders.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_arena + pl->ar.targets, pl->ul.targets.data(),
+                   sizeof(TargetDesc) * pl->ul.targets.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
     e = cudaMemset(pl->d_arena + pl->ar.done, 0, sizeof(uint32_t) * pl->ul.units.size());
   if (e != cudaSuccess) {
     cudaFree(pl->d_arena);
@@ -488,9 +535,9 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   }
   pl->grid = persistent_grid(ctx, pl->ul.emin, pl->ul.emax);
   ccm_plan_info& in = pl->info;
-  in.n_units = (int64_t)pl->ul.units.size();
+  in.n_units = pl->ul.n_rho;
   in.n_queries = pl->ul.q_total;
-  in.library_entries = pl->ul.lib_total;
+  in.library_entries = pl->ul.lib_dbg_total;
   in.neighbour_entries = pl->ul.nbr_total;
   in.n_work_items = (int64_t)pl->ul.items.size();
   in.device_bytes = pl->ar.total;
@@ -539,43 +586,37 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
   if (want_dbg) {
     // Checking path: direct launches with the per-unit outputs (no graph).
     const UnitList& ul = plan->ul;
-    std::vector<int64_t> lib_off(ul.units.size());
-    for (size_t q = 0; q < ul.units.size(); ++q) lib_off[q] = ul.units[q].lib_off;
-    const size_t lb = sizeof(int32_t) * (size_t)ul.lib_total;
+    const size_t lb = sizeof(int32_t) * (size_t)ul.lib_dbg_total;
     const size_t nb = sizeof(int32_t) * (size_t)ul.nbr_total;
     const size_t xb = sizeof(float) * (size_t)ul.q_total;
-    const size_t ob = sizeof(int64_t) * lib_off.size();
     char* tmp = nullptr;
-    const size_t tmp_bytes = align_up(ob, 256) + (out_dev ? 0 : align_up(lb, 256) +
-                                                  align_up(nb, 256) + align_up(xb, 256));
-    CCM_CUDA(cudaMallocAsync(&tmp, tmp_bytes, s));
-    int64_t* d_off = reinterpret_cast<int64_t*>(tmp);
-    char* t2 = tmp + align_up(ob, 256);
-    int32_t* d_lib = dbg->libraries ? (out_dev ? dbg->libraries : reinterpret_cast<int32_t*>(t2))
+    if (!out_dev) {
+      CCM_CUDA(cudaMallocAsync(&tmp, align_up(lb, 256) + align_up(nb, 256) + align_up(xb, 256), s));
+    }
+    int32_t* d_lib = dbg->libraries ? (out_dev ? dbg->libraries : reinterpret_cast<int32_t*>(tmp))
                                     : nullptr;
     int32_t* d_nbr = dbg->neighbours ? (out_dev ? dbg->neighbours
-                                                : reinterpret_cast<int32_t*>(t2 + align_up(lb, 256)))
+                                                : reinterpret_cast<int32_t*>(tmp + align_up(lb, 256)))
                                      : nullptr;
     float* d_xh = dbg->predictions
                       ? (out_dev ? dbg->predictions
-                                 : reinterpret_cast<float*>(t2 + align_up(lb, 256) + align_up(nb, 256)))
+                                 : reinterpret_cast<float*>(tmp + align_up(lb, 256) + align_up(nb, 256)))
                       : nullptr;
-    CCM_CUDA(cudaMemcpyAsync(d_off, lib_off.data(), ob, cudaMemcpyHostToDevice, s));
     ccm_status st =
-        enqueue_sweep(base, plan->ar, ul, plan->grid, 1, d_lib, d_off, d_nbr, d_xh, s, plan->ev);
+        enqueue_sweep(base, plan->ar, ul, plan->grid, 1, d_lib, d_nbr, d_xh, s, plan->ev);
     if (st != CCM_OK) return st;
     if (!out_dev) {
       if (dbg->libraries) CCM_CUDA(cudaMemcpyAsync(dbg->libraries, d_lib, lb, cudaMemcpyDeviceToHost, s));
       if (dbg->neighbours) CCM_CUDA(cudaMemcpyAsync(dbg->neighbours, d_nbr, nb, cudaMemcpyDeviceToHost, s));
       if (dbg->predictions) CCM_CUDA(cudaMemcpyAsync(dbg->predictions, d_xh, xb, cudaMemcpyDeviceToHost, s));
+      CCM_CUDA(cudaFreeAsync(tmp, s));
     }
-    CCM_CUDA(cudaFreeAsync(tmp, s));
   } else {
     if (!plan->graph) {
       cudaGraph_t graph = nullptr;
       CCM_CUDA(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
       ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->grid, 1, nullptr, nullptr,
-                                    nullptr, nullptr, plan->stream, plan->ev, true);
+                                    nullptr, plan->stream, plan->ev, true);
       const cudaError_t ce = cudaStreamEndCapture(plan->stream, &graph);
       if (st != CCM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -588,7 +629,7 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
     }
     CCM_CUDA(cudaGraphLaunch(plan->graph, s));
   }
-  const size_t rho_bytes = sizeof(double) * plan->ul.units.size();
+  const size_t rho_bytes = sizeof(double) * (size_t)plan->ul.n_rho;
   CCM_CUDA(cudaMemcpyAsync(rho, base + plan->ar.rho, rho_bytes,
                            out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   if (!cuda_stream || !in_dev || !out_dev) return check_err_flag(base, plan->ar, s);
@@ -627,16 +668,22 @@ ccm_status ccm_run_plain(ccm_plan_t* plan, const float* series, double* rho, voi
   CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
   const SamplerParams sp = sampler_params(base, ar);
   const UnitDesc* d_units = reinterpret_cast<const UnitDesc*>(base + ar.units);
+  const TargetDesc* d_targets = reinterpret_cast<const TargetDesc*>(base + ar.targets);
+  CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
+                        reinterpret_cast<const OrderJob*>(base + ar.orders),
+                        (int64_t)plan->ul.orders.size(), plan->ul.max_nm,
+                        reinterpret_cast<int32_t*>(base + ar.order), s));
   for (size_t q = 0; q < plan->ul.units.size(); ++q) {
     const UnitDesc& u = plan->ul.units[q];
     CCM_CUDA(launch_sampler(sp, (int64_t)q, 1, u.n_m, s));
-    CCM_CUDA(launch_plain_unit(reinterpret_cast<const float*>(base + ar.series), d_units + q, u,
-                               reinterpret_cast<const int32_t*>(base + ar.lib),
-                               reinterpret_cast<float*>(base + ar.scratch),
-                               reinterpret_cast<double*>(base + ar.rho), nullptr, nullptr,
-                               reinterpret_cast<int32_t*>(base + ar.err), s));
+    for (int32_t t = 0; t < u.n_targets; ++t)
+      CCM_CUDA(launch_plain_unit(reinterpret_cast<const float*>(base + ar.series), d_units + q, u,
+                                 d_targets + u.tgt_off + t,
+                                 reinterpret_cast<const int32_t*>(base + ar.lib),
+                                 reinterpret_cast<float*>(base + ar.scratch),
+                                 reinterpret_cast<double*>(base + ar.rho), s));
   }
-  CCM_CUDA(cudaMemcpyAsync(rho, base + ar.rho, sizeof(double) * plan->ul.units.size(),
+  CCM_CUDA(cudaMemcpyAsync(rho, base + ar.rho, sizeof(double) * (size_t)plan->ul.n_rho,
                            out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   if (!cuda_stream || !in_dev || !out_dev) return check_err_flag(base, ar, s);
   return CCM_OK;
@@ -679,7 +726,7 @@ size_t job_footprint(const ProblemCopy& pc, double* pairs) {
   UnitList ul;
   append_units(pc, 0, 0, &ul);
   *pairs = ul.pairs;
-  return layout((int64_t)pc.V * pc.n, ul, (int64_t)ul.units.size(), 0).total;
+  return layout((int64_t)pc.V * pc.n, ul, ul.n_rho, 0).total;
 }
 
 void CUDART_CB on_batch_done(void* arg) {
@@ -716,20 +763,23 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
   const size_t ub = sizeof(UnitDesc) * b->ul.units.size();
   const size_t ib = sizeof(WorkItem) * b->ul.items.size();
   const size_t ob = sizeof(OrderJob) * b->ul.orders.size();
-  b->meta_bytes = ub + ib + ob;
+  const size_t tb = sizeof(TargetDesc) * b->ul.targets.size();
+  b->meta_bytes = ub + ib + ob + tb;
   b->h_meta = pinned_get(ctx, b->meta_bytes);
   if (!b->h_meta) return fail(CCM_ENOMEM, "pinned allocation failed");
   char* hm = static_cast<char*>(b->h_meta);
   std::memcpy(hm, b->ul.units.data(), ub);
   std::memcpy(hm + ub, b->ul.items.data(), ib);
   std::memcpy(hm + ub + ib, b->ul.orders.data(), ob);
+  std::memcpy(hm + ub + ib + ob, b->ul.targets.data(), tb);
   CCM_CUDA(cudaMemcpyAsync(base + b->ar.units, hm, ub, cudaMemcpyHostToDevice, b->stream));
   CCM_CUDA(cudaMemcpyAsync(base + b->ar.items, hm + ub, ib, cudaMemcpyHostToDevice, b->stream));
   CCM_CUDA(cudaMemcpyAsync(base + b->ar.orders, hm + ub + ib, ob, cudaMemcpyHostToDevice,
                            b->stream));
+  CCM_CUDA(cudaMemcpyAsync(base + b->ar.targets, hm + ub + ib + ob, tb, cudaMemcpyHostToDevice,
+                           b->stream));
   CCM_CUDA(cudaMemsetAsync(base + b->ar.done, 0, sizeof(uint32_t) * b->ul.units.size(), b->stream));
-  ccm_status st = enqueue_sweep(base, b->ar, b->ul, 0, 0, nullptr, nullptr, nullptr, nullptr,
-                                b->stream);
+  ccm_status st = enqueue_sweep(base, b->ar, b->ul, 0, 0, nullptr, nullptr, nullptr, b->stream);
   if (st != CCM_OK) return st;
   int64_t ro = 0;
   for (auto& j : b->jobs) {

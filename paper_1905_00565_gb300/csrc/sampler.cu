@@ -144,7 +144,6 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
     return;
   }
   int32_t* out = p.lib + u.lib_off;
-  int32_t* dbg = p.dbg_lib ? p.dbg_lib + p.dbg_lib_off[uidx] : nullptr;
   uint32_t w = out_before, tie_seen = tie_before;
   for (int m = m0; m < m1; ++m) {
     const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
@@ -155,7 +154,9 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
     }
     if (take) {
       out[w] = m;
-      if (dbg) dbg[w] = m;
+      if (p.dbg_lib)  // checking copy, once per target of this library
+        for (int t = 0; t < u.n_targets; ++t)
+          p.dbg_lib[p.targets[u.tgt_off + t].lib_dbg_off + w] = m;
       ++w;
     }
   }
