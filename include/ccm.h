@@ -63,6 +63,7 @@ typedef enum {
 /* ccm_problem.flags */
 #define CCM_INPUT_ON_DEVICE  0x1u  /* series pointers given to ccm_run are device memory */
 #define CCM_OUTPUT_ON_DEVICE 0x2u  /* rho (and debug outputs) given to ccm_run are device memory */
+#define CCM_NO_AUTOTUNE      0x4u  /* keep cached or default kernel parameters (see ccm_run) */
 
 typedef struct {
   int32_t n_series;        /* V >= 2 series, each of length n */
@@ -129,7 +130,14 @@ ccm_status ccm_plan_get_info(const ccm_plan_t* plan, ccm_plan_info* info);
  * NULL to run on the plan's own stream and block until done.  With a caller
  * stream and device output the call is asynchronous; with host input or
  * output it synchronises the stream before returning.  Host series are
- * checked for non-finite values (CCM_EINVAL). */
+ * checked for non-finite values (CCM_EINVAL).
+ * Autotuning: on the first ccm_run of a plan with at least 2e11 query-library
+ * pairs, for every E whose parameters are not yet known to the context, the
+ * library times two kernel variants and three merge triggers on a sample of
+ * the plan's work items and keeps the fastest (results are identical for all
+ * of them).  Choices are cached per (device name, E) in $CCM_AUTOTUNE_CACHE,
+ * default ~/.cache/ccm_gb300/autotune.tsv, and loaded by ccm_context_create.
+ * CCM_NO_AUTOTUNE skips the measurement. */
 ccm_status ccm_run(ccm_plan_t* plan, const float* series, double* rho, void* cuda_stream);
 
 /* ccm_run plus optional per-unit outputs (dbg may be NULL). */

@@ -33,6 +33,7 @@ CCM_ECANCELLED = -6
 CCM_ENOTFOUND = -7
 CCM_INPUT_ON_DEVICE = 0x1
 CCM_OUTPUT_ON_DEVICE = 0x2
+CCM_NO_AUTOTUNE = 0x4
 
 STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM",
                 -3: "CCM_ETOOLARGE", -4: "CCM_ECUDA", -5: "CCM_ETIMEOUT",

@@ -81,10 +81,12 @@ struct KnnParams {
   int32_t* err;
   int32_t persistent;     // 1: CTAs pull items from item_counter; 0: item = blockIdx.x
   int32_t merge_at[kMaxE + 1];  // per E: merge pending candidates once a lane holds this many
+  int32_t variant[kMaxE + 1];   // per E: kernel variant (0 narrow, 1 wide); same results
 };
 
-// Default merge trigger per E (pending candidates per lane), before tuning.
+// Defaults before tuning: merge trigger (pending candidates per lane) and variant.
 constexpr int kDefaultMergeAt = 9;
+constexpr int kDefaultVariant = 1;
 
 // Error flag values written by kernels.
 constexpr int32_t kErrBadUnit = 1;

@@ -45,39 +45,30 @@ constexpr int kThreads = 256;             // threads per CTA = queries per tile
 constexpr int kQT = kThreads;             // queries per tile (one per thread)
 constexpr int kBuf = 16;                  // pending candidates per query
 constexpr int kCoordBytes = 40 * 1024;    // shared memory for one library tile
-#ifndef CCM_STEP_SMALL_E
-#define CCM_STEP_SMALL_E 8
-#endif
-#ifndef CCM_STEP_LARGE_E
-#define CCM_STEP_LARGE_E 4
-#endif
-#ifndef CCM_STEP_SPLIT_E
-#define CCM_STEP_SPLIT_E 6
-#endif
-#ifndef CCM_EARLY_MIN_E
-#define CCM_EARLY_MIN_E 3
-#endif
-// Library points per step (two points per packed operand): more points give
-// more independent FMA chains per warp; large E is limited by registers.
-template <int E>
-constexpr int kStepE = (E <= CCM_STEP_SPLIT_E) ? CCM_STEP_SMALL_E : CCM_STEP_LARGE_E;
 constexpr int kBufBytes = kBuf * kThreads * 8;
 constexpr int kSmemBytes = kCoordBytes + kBufBytes;
 constexpr unsigned kFull = 0xffffffffu;
+// Kernel variants picked per E by the autotuner (results are identical):
+//   V = 0 "narrow": 4 library points per step, no early termination;
+//   V = 1 "wide":   8 points per step and, for E = 3..6, early termination
+//                   (E <= 6 only: above, registers run out and the two coincide).
+constexpr int kVariants = 2;
 
-#ifndef CCM_EARLY_MAX_E
-#define CCM_EARLY_MAX_E 6
-#endif
+// Library points per step (two points per packed operand): more points give
+// more independent FMA chains per warp.
+template <int E, int V>
+constexpr int kStepE = (V == 1 && E <= 6) ? 8 : 4;
+
 // Coordinates summed before the early-termination check (E when there is none).
-template <int E>
-constexpr int kE1 = (E < CCM_EARLY_MIN_E || E > CCM_EARLY_MAX_E || E <= 2) ? E : 2;
+template <int E, int V>
+constexpr int kE1 = (V == 1 && E >= 3 && E <= 6) ? 2 : E;
 
 template <int E>
 struct TileShape {
   static constexpr int EP = E + (E & 1);                        // coordinates padded to even
   // library points per tile: a point pair takes EP*8 bytes of coordinates + 8 of indices
   static constexpr int LT = (kCoordBytes / (EP * 8 + 8)) * 2 / 64 * 64;
-  static_assert(LT >= 64 && LT % kStepE<E> == 0, "tile must hold whole steps");
+  static_assert(LT >= 64 && LT % 8 == 0, "tile must hold whole steps");
 };
 
 __device__ __forceinline__ u64 pack2(float a, float b) {
@@ -195,7 +186,7 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
   __syncthreads();
 }
 
-template <int E>
+template <int E, int V>
 __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, int tile,
                              unsigned char* smem, double* s_red, int* s_last) {
   constexpr int K = E + 2;
@@ -211,7 +202,7 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
   const int32_t* lib = p.lib + u.lib_off;
   const int32_t* order = p.order + u.order_off;
-  constexpr int kStep = kStepE<E>;
+  constexpr int kStep = kStepE<E, V>;
   constexpr int kPairs = kStep / 2;
   // merge trigger: at most kBuf - kStep + 1 so that a step can always append
   const int merge_at = max(1, min(p.merge_at[E], kBuf - kStep + 1));
@@ -277,16 +268,16 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
       // contribute a candidate and skips the remaining coordinates.
       u64 r[kPairs];
 #pragma unroll
-      for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, kE1<E>>(qc, cp + pp * EP, 0ull);
+      for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, (kE1<E, V>)>(qc, cp + pp * EP, 0ull);
       const float th = kd[K - 1];
       float d[kStep];
 #pragma unroll
       for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
       if (!__any_sync(kFull, min_all(d) < th)) continue;
-      if constexpr (kE1<E> < E) {
+      if constexpr ((kE1<E, V>) < E) {
 #pragma unroll
         for (int pp = 0; pp < kPairs; ++pp) {
-          r[pp] = sqdist2_range<E, kE1<E>, E>(qc, cp + pp * EP, r[pp]);
+          r[pp] = sqdist2_range<E, (kE1<E, V>), E>(qc, cp + pp * EP, r[pp]);
           unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
         }
         if (!__any_sync(kFull, min_all(d) < th)) continue;
@@ -411,7 +402,14 @@ __device__ __forceinline__ bool dispatch(int E, const KnnParams& p, const UnitDe
 #define CCM_CASE(EV)                                                    \
   if constexpr (EV >= EMIN && EV <= EMAX) {                             \
     if (E == EV) {                                                      \
-      process_tile<EV>(p, u, unit, tile, smem, s_red, s_last);          \
+      if constexpr (EV <= 6) {                                          \
+        if (p.variant[EV] == 1)                                         \
+          process_tile<EV, 1>(p, u, unit, tile, smem, s_red, s_last);   \
+        else                                                            \
+          process_tile<EV, 0>(p, u, unit, tile, smem, s_red, s_last);   \
+      } else {                                                          \
+        process_tile<EV, 0>(p, u, unit, tile, smem, s_red, s_last);     \
+      }                                                                 \
       ok = true;                                                        \
     }                                                                   \
   }

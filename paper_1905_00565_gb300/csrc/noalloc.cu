@@ -220,7 +220,10 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   kp.rho = d_rho;
   kp.err = reinterpret_cast<int32_t*>(scratch + lay.err);
   kp.persistent = 0;
-  for (int q = 0; q <= kMaxE; ++q) kp.merge_at[q] = kDefaultMergeAt;
+  for (int q = 0; q <= kMaxE; ++q) {
+    kp.merge_at[q] = kDefaultMergeAt;
+    kp.variant[q] = kDefaultVariant;
+  }
   e = launch_knn(kp, E, E, (int)kp.n_items, s);
   if (e != cudaSuccess) return noalloc_fail(CCM_ECUDA, cudaGetErrorString(e));
   if (!cuda_stream) {

@@ -18,6 +18,7 @@
 #include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
+#include <sys/stat.h>
 #include <cstring>
 #include <deque>
 #include <list>
@@ -287,12 +288,31 @@ namespace ccm {
 void set_last_error(const char* msg) { t_err = msg; }
 }  // namespace ccm
 
+// Per-E kernel parameters chosen by the autotuner (results do not depend on them).
+struct Tuning {
+  int32_t variant[kMaxE + 1];
+  int32_t merge_at[kMaxE + 1];
+  bool known[kMaxE + 1];  // chosen by measurement (here or from the cache)
+};
+
+Tuning default_tuning() {
+  Tuning t;
+  for (int e = 0; e <= kMaxE; ++e) {
+    t.variant[e] = kDefaultVariant;
+    t.merge_at[e] = kDefaultMergeAt;
+    t.known[e] = false;
+  }
+  return t;
+}
+
 // ================================================================ context ===
 struct Job;
 struct Batch;
 
 struct ccm_context {
   int device = 0;
+  std::string device_name;
+  Tuning tuning = default_tuning();  // per-E choices known to this context (cache + runs)
   size_t budget = 0;
   size_t used = 0;
   int sm_count = 0;
@@ -378,6 +398,8 @@ struct ccm_plan_s {
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before sampler, before knn, after knn
   int grid = 0;
+  Tuning tuning = default_tuning();
+  bool tuned = false;
   std::mutex run_mu;
   ccm_plan_info info{};
 };
@@ -393,7 +415,8 @@ SamplerParams sampler_params(char* base, const Arena& ar) {
   return sp;
 }
 
-KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persistent) {
+KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persistent,
+                     const Tuning& tn) {
   KnnParams kp{};
   kp.series = reinterpret_cast<const float*>(base + ar.series);
   kp.units = reinterpret_cast<const UnitDesc*>(base + ar.units);
@@ -408,16 +431,17 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.rho = reinterpret_cast<double*>(base + ar.rho);
   kp.err = reinterpret_cast<int32_t*>(base + ar.err);
   kp.persistent = persistent;
-  for (int e = 0; e <= kMaxE; ++e) kp.merge_at[e] = kDefaultMergeAt;
-  if (const char* env = getenv("CCM_MERGE_AT"))
-    for (int e = 0; e <= kMaxE; ++e) kp.merge_at[e] = atoi(env);
+  for (int e = 0; e <= kMaxE; ++e) {
+    kp.merge_at[e] = tn.merge_at[e];
+    kp.variant[e] = tn.variant[e];
+  }
   return kp;
 }
 
 // Enqueue sampler + fused kernel for a whole unit list on stream s.
-ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int grid, int persistent,
-                         int32_t* dbg_lib, int32_t* dbg_nbr, float* dbg_xhat, cudaStream_t s,
-                         cudaEvent_t* ev = nullptr,
+ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const Tuning& tn,
+                         int grid, int persistent, int32_t* dbg_lib, int32_t* dbg_nbr,
+                         float* dbg_xhat, cudaStream_t s, cudaEvent_t* ev = nullptr,
                          bool capturing = false) {
   // Inside stream capture an event record becomes a graph node only with the
   // external flag; outside capture the plain record is the valid form.
@@ -436,7 +460,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, int gr
                         (int64_t)ul.orders.size(), ul.max_nm,
                         reinterpret_cast<int32_t*>(base + ar.order), s));
   CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
-  KnnParams kp = knn_params(base, ar, ul, persistent);
+  KnnParams kp = knn_params(base, ar, ul, persistent, tn);
   kp.dbg_nbr = dbg_nbr;
   kp.dbg_xhat = dbg_xhat;
   const int g = persistent ? grid : (int)ul.items.size();
@@ -458,6 +482,133 @@ int persistent_grid(ccm_context* ctx, int emin, int emax) {
   int per_sm = 1;
   if (knn_occupancy(emin, emax, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
   return ctx->sm_count * per_sm;
+}
+
+}  // namespace
+
+// ============================================================== autotuner ===
+namespace {
+
+// Per E the tuner times the kernel variants (narrow / wide) and merge triggers
+// on a stratified sample of the plan's own work items and keeps the fastest.
+// Every candidate computes the same result; only the time differs.  Choices
+// are cached per (device name, E) in a tab-separated file: $CCM_AUTOTUNE_CACHE,
+// else ~/.cache/ccm_gb300/autotune.tsv.
+std::string cache_path() {
+  if (const char* p = getenv("CCM_AUTOTUNE_CACHE")) return p;
+  const char* home = getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/ccm_gb300/autotune.tsv";
+}
+
+void load_cache(ccm_context* ctx) {
+  FILE* f = fopen(cache_path().c_str(), "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    char name[256];
+    int E = 0, v = 0, ma = 0;
+    if (sscanf(line, "%255[^\t]\t%d\t%d\t%d", name, &E, &v, &ma) == 4 &&
+        ctx->device_name == name && E >= 1 && E <= kMaxE && v >= 0 && v <= 1 && ma >= 1 &&
+        ma <= 16) {
+      ctx->tuning.variant[E] = v;
+      ctx->tuning.merge_at[E] = ma;
+      ctx->tuning.known[E] = true;
+    }
+  }
+  fclose(f);
+}
+
+void save_cache(const ccm_context* ctx, int E, int v, int ma) {
+  const std::string path = cache_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {  // mkdir -p of the parent, best effort
+    std::string dir = path.substr(0, slash);
+    for (size_t q = 1; q <= dir.size(); ++q)
+      if (q == dir.size() || dir[q] == '/') {
+        const std::string d = dir.substr(0, q);
+        (void)mkdir(d.c_str(), 0755);
+      }
+  }
+  FILE* f = fopen(path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "%s\t%d\t%d\t%d\n", ctx->device_name.c_str(), E, v, ma);
+  fclose(f);
+}
+
+constexpr double kTunePairs = 2.0e11;   // plans smaller than this use known or default choices
+
+ccm_status autotune(ccm_plan_s* pl, cudaStream_t s) {
+  ccm_context* ctx = pl->ctx;
+  char* base = pl->d_arena;
+  const Arena& ar = pl->ar;
+  const UnitList& ul = pl->ul;
+  // libraries and query orders for the timing launches
+  CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
+                        reinterpret_cast<const OrderJob*>(base + ar.orders),
+                        (int64_t)ul.orders.size(), ul.max_nm,
+                        reinterpret_cast<int32_t*>(base + ar.order), s));
+  SamplerParams sp = sampler_params(base, ar);
+  CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
+  const int want = 6 * ctx->sm_count;
+  WorkItem* d_items = nullptr;
+  CCM_CUDA(cudaMallocAsync(&d_items, sizeof(WorkItem) * (size_t)want, s));
+  cudaEvent_t e0, e1;
+  CCM_CUDA(cudaEventCreate(&e0));
+  CCM_CUDA(cudaEventCreate(&e1));
+  ccm_status st = CCM_OK;
+  for (int E = ul.emin; E <= ul.emax && st == CCM_OK; ++E) {
+    if (pl->tuning.known[E]) continue;
+    std::vector<WorkItem> all;
+    for (const WorkItem& w : ul.items)
+      if (ul.units[(size_t)w.unit].E == E) all.push_back(w);
+    if ((int)all.size() < want) continue;
+    std::vector<WorkItem> sample;  // evenly spaced over the cost-sorted list
+    for (int q = 0; q < want; ++q) sample.push_back(all[(size_t)q * all.size() / (size_t)want]);
+    cudaError_t ce = cudaMemcpyAsync(d_items, sample.data(), sizeof(WorkItem) * sample.size(),
+                                     cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) { st = fail(CCM_ECUDA, cudaGetErrorString(ce)); break; }
+    float best = 1e30f;
+    int best_v = pl->tuning.variant[E], best_ma = pl->tuning.merge_at[E];
+    for (int v = 0; v <= (E <= 6 ? 1 : 0); ++v)
+      for (int ma : {3, 6, 9}) {
+        Tuning tn = pl->tuning;
+        tn.variant[E] = v;
+        tn.merge_at[E] = ma;
+        KnnParams kp = knn_params(base, ar, ul, 0, tn);
+        kp.items = d_items;
+        kp.n_items = (int64_t)sample.size();
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {  // warm-up, then timed
+          ce = cudaEventRecord(e0, s);
+          if (ce == cudaSuccess) ce = launch_knn(kp, ul.emin, ul.emax, (int)sample.size(), s);
+          if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+          if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ce != cudaSuccess) break;
+        if (ms < best) {
+          best = ms;
+          best_v = v;
+          best_ma = ma;
+        }
+      }
+    if (ce != cudaSuccess) { st = fail(CCM_ECUDA, cudaGetErrorString(ce)); break; }
+    pl->tuning.variant[E] = best_v;
+    pl->tuning.merge_at[E] = best_ma;
+    pl->tuning.known[E] = true;
+    {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      ctx->tuning.variant[E] = best_v;
+      ctx->tuning.merge_at[E] = best_ma;
+      ctx->tuning.known[E] = true;
+    }
+    save_cache(ctx, E, best_v, best_ma);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(d_items, s);
+  if (st == CCM_OK) CCM_CUDA(cudaStreamSynchronize(s));
+  return st;
 }
 
 }  // namespace
@@ -486,7 +637,9 @@ ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context**
   CCM_CUDA(cudaMemGetInfo(&free_b, &total_b));
   std::unique_ptr<ccm_context> ctx(new ccm_context());
   ctx->device = device;
+  ctx->device_name = prop.name;
   ctx->sm_count = prop.multiProcessorCount;
+  load_cache(ctx.get());
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
   *out = ctx.release();
   return CCM_OK;
@@ -534,6 +687,10 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
     return fail(CCM_ECUDA, std::string("plan set-up: ") + cudaGetErrorString(e));
   }
   pl->grid = persistent_grid(ctx, pl->ul.emin, pl->ul.emax);
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    pl->tuning = ctx->tuning;
+  }
   ccm_plan_info& in = pl->info;
   in.n_units = pl->ul.n_rho;
   in.n_queries = pl->ul.q_total;
@@ -603,7 +760,8 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
                                  : reinterpret_cast<float*>(tmp + align_up(lb, 256) + align_up(nb, 256)))
                       : nullptr;
     ccm_status st =
-        enqueue_sweep(base, plan->ar, ul, plan->grid, 1, d_lib, d_nbr, d_xh, s, plan->ev);
+        enqueue_sweep(base, plan->ar, ul, plan->tuning, plan->grid, 1, d_lib, d_nbr, d_xh, s,
+                      plan->ev);
     if (st != CCM_OK) return st;
     if (!out_dev) {
       if (dbg->libraries) CCM_CUDA(cudaMemcpyAsync(dbg->libraries, d_lib, lb, cudaMemcpyDeviceToHost, s));
@@ -612,11 +770,21 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
       CCM_CUDA(cudaFreeAsync(tmp, s));
     }
   } else {
+    if (!plan->tuned) {
+      bool missing = false;
+      for (int e = plan->ul.emin; e <= plan->ul.emax; ++e)
+        for (const int32_t E : pc.E) missing |= (E == e && !plan->tuning.known[e]);
+      if (missing && !(pc.flags & CCM_NO_AUTOTUNE) && plan->ul.pairs >= kTunePairs) {
+        ccm_status st = autotune(plan, s);
+        if (st != CCM_OK) return st;
+      }
+      plan->tuned = true;
+    }
     if (!plan->graph) {
       cudaGraph_t graph = nullptr;
       CCM_CUDA(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
-      ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->grid, 1, nullptr, nullptr,
-                                    nullptr, plan->stream, plan->ev, true);
+      ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->tuning, plan->grid, 1,
+                                    nullptr, nullptr, nullptr, plan->stream, plan->ev, true);
       const cudaError_t ce = cudaStreamEndCapture(plan->stream, &graph);
       if (st != CCM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -779,7 +947,13 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
   CCM_CUDA(cudaMemcpyAsync(base + b->ar.targets, hm + ub + ib + ob, tb, cudaMemcpyHostToDevice,
                            b->stream));
   CCM_CUDA(cudaMemsetAsync(base + b->ar.done, 0, sizeof(uint32_t) * b->ul.units.size(), b->stream));
-  ccm_status st = enqueue_sweep(base, b->ar, b->ul, 0, 0, nullptr, nullptr, nullptr, b->stream);
+  Tuning tn;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    tn = ctx->tuning;
+  }
+  ccm_status st =
+      enqueue_sweep(base, b->ar, b->ul, tn, 0, 0, nullptr, nullptr, nullptr, b->stream);
   if (st != CCM_OK) return st;
   int64_t ro = 0;
   for (auto& j : b->jobs) {
