@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=40)
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run every sweep cell with R realizations through ccm_run "
@@ -304,6 +305,10 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "rho_finite": rho_ok,
         }
+        if not args.no_table:
+            tv = table_variant(ccm, ctx, p, torch, args.steps, 1, rho_dev, flush, stream)
+            tv["speedup_vs_brute_force"] = tv["value"] / out["value"]
+            out["table_variant"] = tv
         if not args.no_plain:
             out["vs_plain_gpu"] = compare_plain(ccm, ctx, I, p, torch)
         if not args.no_serving:
@@ -363,6 +368,42 @@ def serve_stream(ccm, I, n_jobs: int, device: int):
             "max_latency_ms": float(lat.max() * 1e3),
             "realizations_per_s": units / span2, "pairs": float(pairs),
             "makespan_s": span2}
+
+
+def table_variant(ccm, ctx, p, torch, steps: int, warmup: int, rho_ref, flush, stream):
+    """The same sweep with distance indexing tables (paper Sect. 3.2): large-L
+    realizations read their neighbours from per-(variable, E, tau) tables of
+    each point's nearest points; results are bit-identical to brute force."""
+    flags = ccm.CCM_INPUT_ON_DEVICE | ccm.CCM_OUTPUT_ON_DEVICE | ccm.CCM_TABLE
+    plan = ccm.plan_problem(ctx, p, flags)
+    info = ccm.ccm_plan_get_info(plan)
+    s_dev = torch.from_numpy(p.series).cuda()
+    rho = torch.zeros(ccm.rho_shape(p), dtype=torch.float64, device="cuda")
+    for _ in range(max(1, warmup)):
+        ccm.ccm_run(plan, s_dev, rho, stream=stream)
+        stream.synchronize()
+    step_ms, stages = [], []
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ccm.ccm_run(plan, s_dev, rho, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stages.append(ccm.ccm_plan_stage_times(plan))
+    same = bool(torch.equal(rho, rho_ref))
+    ccm.ccm_plan_destroy(plan)
+    t = sum(step_ms) / len(step_ms)
+    st = [sum(x[q] for x in stages) / len(stages) for q in range(4)]
+    return {"value": info["n_units"] / (t / 1e3), "unit": UNIT, "ms_per_step": t,
+            "stage_ms": {"order_and_tables": st[0], "sampler": st[1], "brute_force_knn": st[2],
+                         "table_scan_knn": st[3]},
+            "table_bytes": info["table_bytes"],
+            "brute_force_share_of_flops": info["brute_flop_count"] / info["flop_count"],
+            "same_rho_bits_as_brute_force": same}
 
 
 def compare_plain(ccm, ctx, I, p, torch):

@@ -64,6 +64,8 @@ typedef enum {
 #define CCM_INPUT_ON_DEVICE  0x1u  /* series pointers given to ccm_run are device memory */
 #define CCM_OUTPUT_ON_DEVICE 0x2u  /* rho (and debug outputs) given to ccm_run are device memory */
 #define CCM_NO_AUTOTUNE      0x4u  /* keep cached or default kernel parameters (see ccm_run) */
+#define CCM_TABLE            0x8u  /* large-L realizations read neighbours from distance
+                                      indexing tables (paper Sect. 3.2); same results */
 
 typedef struct {
   int32_t n_series;        /* V >= 2 series, each of length n */
@@ -101,6 +103,8 @@ typedef struct {
   size_t device_bytes;        /* device footprint of the plan */
   double pair_count;          /* query-library pairs = sum over units of N_m*L */
   double flop_count;          /* 3E FP32 flops per pair, summed */
+  double brute_flop_count;    /* the part of flop_count searched by brute force */
+  size_t table_bytes;         /* distance indexing tables (CCM_TABLE), 0 without */
 } ccm_plan_info;
 
 typedef struct ccm_context ccm_context;
@@ -144,10 +148,16 @@ ccm_status ccm_run(ccm_plan_t* plan, const float* series, double* rho, void* cud
 ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho,
                       const ccm_debug_out* dbg, void* cuda_stream);
 
-/* Device time of the sampler launch and of the fused kNN launch in the plan's
+/* Device time of the preparation launches (query order, tables, sampler) and
+ * of the neighbour-search launches (brute force + table scan) in the plan's
  * last completed ccm_run / ccm_run_ex (CUDA events recorded on the run's
  * stream around each launch).  Call after that run has finished. */
 ccm_status ccm_plan_kernel_times(const ccm_plan_t* plan, double* sampler_ms, double* knn_ms);
+
+/* The same events per stage: stage_ms[0] query order + distance indexing
+ * tables, [1] library sampler, [2] brute-force fused kernel, [3] table-scan
+ * fused kernel (0 when the stage launched nothing). */
+ccm_status ccm_plan_stage_times(const ccm_plan_t* plan, double* stage_ms /* [4] */);
 
 /* The plain comparator: one sampler launch and one naive kNN launch per
  * realization (thread per query, library read from global memory, sorted

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libccm_gb300.so")
-SOURCES = ["runtime.cu", "sampler.cu", "knn_fused.cu", "plain.cu", "noalloc.cu", "order.cu"]
+SOURCES = ["runtime.cu", "sampler.cu", "knn_fused.cu", "plain.cu", "noalloc.cu", "order.cu",
+           "table.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

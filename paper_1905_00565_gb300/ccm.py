@@ -34,6 +34,7 @@ CCM_ENOTFOUND = -7
 CCM_INPUT_ON_DEVICE = 0x1
 CCM_OUTPUT_ON_DEVICE = 0x2
 CCM_NO_AUTOTUNE = 0x4
+CCM_TABLE = 0x8
 
 STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM",
                 -3: "CCM_ETOOLARGE", -4: "CCM_ECUDA", -5: "CCM_ETIMEOUT",
@@ -43,7 +44,7 @@ STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM
 EXPORTED = ["ccm_context_create", "ccm_context_destroy", "ccm_plan", "ccm_plan_destroy",
             "ccm_plan_get_info", "ccm_run", "ccm_run_ex", "ccm_run_plain", "ccm_submit",
             "ccm_poll", "ccm_cancel", "ccm_job_times", "ccm_last_error", "ccm_version",
-            "ccm_plan_kernel_times", "ccm_run_noalloc"]
+            "ccm_plan_kernel_times", "ccm_run_noalloc", "ccm_plan_stage_times"]
 
 
 class ccm_problem(ctypes.Structure):
@@ -64,7 +65,8 @@ class ccm_plan_info(ctypes.Structure):
     _fields_ = [("n_units", ctypes.c_int64), ("n_queries", ctypes.c_int64),
                 ("library_entries", ctypes.c_int64), ("neighbour_entries", ctypes.c_int64),
                 ("n_work_items", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
-                ("pair_count", ctypes.c_double), ("flop_count", ctypes.c_double)]
+                ("pair_count", ctypes.c_double), ("flop_count", ctypes.c_double),
+                ("brute_flop_count", ctypes.c_double), ("table_bytes", ctypes.c_size_t)]
 
 
 class CCMError(RuntimeError):
@@ -91,6 +93,7 @@ def _load():
         "ccm_run_plain": ([vp, vp, vp, vp], st),
         "ccm_plan_kernel_times": ([vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)], st),
+        "ccm_plan_stage_times": ([vp, ctypes.POINTER(ctypes.c_double)], st),
         "ccm_submit": ([vp, ctypes.POINTER(ccm_problem), vp, ctypes.POINTER(u64)], st),
         "ccm_poll": ([vp, u64, vp, i32], st),
         "ccm_cancel": ([vp, u64], st),
@@ -211,6 +214,13 @@ def ccm_plan_kernel_times(plan: int):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(_lib.ccm_plan_kernel_times(plan, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def ccm_plan_stage_times(plan: int):
+    """[order + tables, sampler, brute-force kNN, table-scan kNN] device ms of the last run."""
+    out = (ctypes.c_double * 4)()
+    _check(_lib.ccm_plan_stage_times(plan, out))
+    return list(out)
 
 
 def ccm_run_plain(plan: int, series, rho, stream=None) -> None:

@@ -20,6 +20,7 @@ struct UnitDesc {
   int64_t part_off;     // first partial-moment slot: target t, tile q at part_off + t*n_tiles + q
   int64_t order_off;    // first entry of this unit's query order (per variable, E, tau)
   int64_t tgt_off;      // first TargetDesc of this unit
+  int64_t table_off;    // distance indexing table of (j, E, tau), when table_R > 0
   uint64_t seed;        // library sampler seed of the job
   int32_t j;            // library variable
   int32_t E, tau;
@@ -27,6 +28,8 @@ struct UnitDesc {
   int32_t n_m;          // manifold points = queries
   int32_t n_tiles;      // query tiles of the fused kernel
   int32_t n_targets;    // targets cross-mapped from this library (>= 1)
+  int32_t table_R;      // > 0: neighbours read from the table (R entries per query)
+  int32_t pad;
 };
 
 // One target of a unit: the pair (j, i) and where its outputs go.
@@ -54,6 +57,18 @@ struct OrderJob {
 };
 constexpr int kOrderMaxSort = 16384;   // manifolds up to this size are sorted
 
+// Distance indexing table job: one per (job, library variable, E, tau) whose
+// realizations read their neighbours from a table.
+struct TableJob {
+  int64_t series_off;   // element offset of the job's series block
+  int64_t n;            // series length
+  int64_t order_off;    // query order of this combination
+  int64_t table_off;    // first entry: table[table_off + r * n_m + pos]
+  int32_t j, E, tau, n_m, R;
+  int32_t pad;
+};
+constexpr int kTableMaxR = 2048;       // entries per query row, at most
+
 // Sampler: one CTA per unit.
 struct SamplerParams {
   const UnitDesc* units;
@@ -72,6 +87,8 @@ struct KnnParams {
   int64_t n_items;
   const int32_t* lib;
   const int32_t* order;   // query order (manifold index per position)
+  const void* table;      // distance indexing tables (units with table_R > 0)
+  int32_t table_u16;      // 1: uint16 entries (every manifold below 65536 points), 0: int32
   double* partials;       // 6 doubles per query tile
   uint32_t* unit_done;    // per-unit tile counters (reset by the unit's last tile)
   uint32_t* item_counter; // dynamic scheduling counter (zeroed before each launch)
@@ -104,6 +121,12 @@ cudaError_t order_prepare();
 cudaError_t launch_order(const float* series, const OrderJob* jobs, int64_t n_jobs, int max_nm,
                          int32_t* order, cudaStream_t s);
 
+// Distance indexing table (table.cu).
+cudaError_t table_prepare();
+cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs,
+                               int max_nm, int max_R, const int32_t* order, void* table,
+                               int table_u16, cudaStream_t s);
+
 // Fused kernel (knn_fused.cu).
 int knn_block_threads();
 int knn_queries_per_thread();
@@ -111,6 +134,11 @@ size_t knn_smem_bytes(int emin, int emax);
 cudaError_t knn_prepare();
 cudaError_t knn_occupancy(int emin, int emax, int* ctas_per_sm);
 cudaError_t launch_knn(const KnnParams& p, int emin, int emax, int grid, cudaStream_t s);
+// Table path: same work items, neighbours read from the distance indexing table.
+size_t knn_table_smem(int max_nm);
+cudaError_t knn_table_prepare(int max_nm);
+cudaError_t knn_table_occupancy(int max_nm, int* ctas_per_sm);
+cudaError_t launch_knn_table(const KnnParams& p, int max_nm, int grid, cudaStream_t s);
 
 // Sets the thread-local message returned by ccm_last_error() (runtime.cu).
 void set_last_error(const char* msg);

@@ -154,13 +154,14 @@ __device__ __forceinline__ void insert_sorted(float (&kd)[K], int (&kl)[K], floa
 }
 
 // Deterministic block sum of three doubles; every thread gets the totals.
+// Explicit round-to-nearest adds: the same bits in every kernel that inlines it.
 __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* s_red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(kFull, a, o);
-    b += __shfl_xor_sync(kFull, b, o);
-    c += __shfl_xor_sync(kFull, c, o);
+    a = __dadd_rn(a, __shfl_xor_sync(kFull, a, o));
+    b = __dadd_rn(b, __shfl_xor_sync(kFull, b, o));
+    c = __dadd_rn(c, __shfl_xor_sync(kFull, c, o));
   }
   if (lane == 0) {
     s_red[3 * warp + 0] = a;
@@ -171,9 +172,9 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
   if (threadIdx.x == 0) {
     double ta = 0.0, tb = 0.0, tc = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) {
-      ta += s_red[3 * w + 0];
-      tb += s_red[3 * w + 1];
-      tc += s_red[3 * w + 2];
+      ta = __dadd_rn(ta, s_red[3 * w + 0]);
+      tb = __dadd_rn(tb, s_red[3 * w + 1]);
+      tc = __dadd_rn(tc, s_red[3 * w + 2]);
     }
     s_red[3 * (kThreads / 32) + 0] = ta;
     s_red[3 * (kThreads / 32) + 1] = tb;
@@ -183,6 +184,109 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
   a = s_red[3 * (kThreads / 32) + 0];
   b = s_red[3 * (kThreads / 32) + 1];
   c = s_red[3 * (kThreads / 32) + 2];
+  __syncthreads();
+}
+
+// Everything after the neighbour search, shared by the brute-force and the
+// table paths: dd[0..E] ascending FP32 squared distances and nb[0..E] the
+// neighbours of query m (itself excluded).  Simplex weights, the prediction
+// of every target, FP64 tile moments, and the in-order merge of the moments
+// by the realization's last tile.
+template <int E>
+__device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& u, int unit,
+                                            int tile, int m, bool valid, const float (&dd)[E + 1],
+                                            const int (&nb)[E + 1], double* s_red, int* s_last) {
+  const int tid = threadIdx.x;
+  const int n_m = u.n_m;
+  const int off = (E - 1) * u.tau;
+  // Simplex weights (Sect. 2.1), once per query for every target.  Every
+  // floating-point step below is an explicit round-to-nearest operation, so
+  // the brute-force and table kernels (and every batch) produce the same bits.
+  const float d1 = __fsqrt_rn(dd[0]);
+  float w[E + 1];
+  int nbc[E + 1];
+  float usum = 0.f;
+#pragma unroll
+  for (int s = 0; s <= E; ++s) {
+    const float di = __fsqrt_rn(dd[s]);
+    w[s] = (d1 > 0.f) ? expf(-__fdiv_rn(di, d1)) : ((di == 0.f) ? 1.f : 0.f);
+    usum = __fadd_rn(usum, w[s]);
+    // an unfilled slot (only possible with non-finite device input) reads in bounds
+    nbc[s] = min(max(nb[s], 0), n_m - 1);
+  }
+
+  for (int t = 0; t < u.n_targets; ++t) {
+    const TargetDesc tg = p.targets[u.tgt_off + t];
+    const float* si = p.series + u.series_off + (int64_t)tg.i * u.n;
+    float acc = 0.f;
+#pragma unroll
+    for (int s = 0; s <= E; ++s) acc = __fmaf_rn(w[s], si[nbc[s] + off], acc);
+    const float xhat = __fdiv_rn(acc, usum);
+    const double xo = valid ? (double)si[m + off] : 0.0;
+    const double xp = valid ? (double)xhat : 0.0;
+    if (valid) {
+      if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
+      if (p.dbg_nbr) {
+#pragma unroll
+        for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nb[s];
+      }
+    }
+    // Tile moments of this target, two passes over the registers.
+    double n = valid ? 1.0 : 0.0, sx = xo, sy = xp;
+    block_sum3(n, sx, sy, s_red);
+    const double mx = __ddiv_rn(sx, n), my = __ddiv_rn(sy, n);
+    double sxx = 0.0, syy = 0.0, sxy = 0.0;
+    if (valid) {
+      const double a = __dsub_rn(xo, mx), b = __dsub_rn(xp, my);
+      sxx = __dmul_rn(a, a);
+      syy = __dmul_rn(b, b);
+      sxy = __dmul_rn(a, b);
+    }
+    block_sum3(sxx, syy, sxy, s_red);
+    if (tid == 0) {
+      double* part = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile);
+      part[0] = n;
+      part[1] = mx;
+      part[2] = my;
+      part[3] = sxx;
+      part[4] = syy;
+      part[5] = sxy;
+    }
+  }
+
+  // The last tile of this realization to finish merges every target's tile
+  // moments in tile order (Chan et al. pairwise update): rho does not depend
+  // on which CTA ran which tile, or when.
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&p.unit_done[unit], 1u);
+    *s_last = (prev == (unsigned)(u.n_tiles - 1)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (*s_last) {
+    __threadfence();
+    for (int t = tid; t < u.n_targets; t += kThreads) {
+      const double* base = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles);
+      double N = __ldcg(base + 0), MX = __ldcg(base + 1), MY = __ldcg(base + 2);
+      double SXX = __ldcg(base + 3), SYY = __ldcg(base + 4), SXY = __ldcg(base + 5);
+      for (int q = 1; q < u.n_tiles; ++q) {
+        const double* pt = base + 6 * q;
+        const double nb2 = __ldcg(pt + 0), mxb = __ldcg(pt + 1), myb = __ldcg(pt + 2);
+        const double tot = __dadd_rn(N, nb2);
+        const double dx = __dsub_rn(mxb, MX), dy = __dsub_rn(myb, MY);
+        const double f = __ddiv_rn(__dmul_rn(N, nb2), tot);
+        SXX = __dadd_rn(SXX, __dadd_rn(__ldcg(pt + 3), __dmul_rn(__dmul_rn(dx, dx), f)));
+        SYY = __dadd_rn(SYY, __dadd_rn(__ldcg(pt + 4), __dmul_rn(__dmul_rn(dy, dy), f)));
+        SXY = __dadd_rn(SXY, __dadd_rn(__ldcg(pt + 5), __dmul_rn(__dmul_rn(dx, dy), f)));
+        MX = __dadd_rn(MX, __ddiv_rn(__dmul_rn(dx, nb2), tot));
+        MY = __dadd_rn(MY, __ddiv_rn(__dmul_rn(dy, nb2), tot));
+        N = tot;
+      }
+      p.rho[p.targets[u.tgt_off + t].out_idx] =
+          (SXX > 0.0 && SYY > 0.0) ? __ddiv_rn(SXY, __dsqrt_rn(__dmul_rn(SXX, SYY))) : nan("");
+    }
+    if (tid == 0) p.unit_done[unit] = 0u;  // ready for the next run
+  }
   __syncthreads();
 }
 
@@ -305,93 +409,143 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
     dd[s] = (s < self) ? kd[s] : kd[s + 1];
     nb[s] = (s < self) ? kl[s] : kl[s + 1];
   }
-  // Simplex weights (Sect. 2.1), once per query for every target.
-  const float d1 = sqrtf(dd[0]);
-  float w[E + 1];
-  int nbc[E + 1];
-  float usum = 0.f;
-#pragma unroll
-  for (int s = 0; s <= E; ++s) {
-    const float di = sqrtf(dd[s]);
-    w[s] = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
-    usum += w[s];
-    // an unfilled slot (only possible with non-finite device input) reads in bounds
-    nbc[s] = min(max(nb[s], 0), n_m - 1);
-  }
+  finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, s_red, s_last);
+}
 
-  for (int t = 0; t < u.n_targets; ++t) {
-    const TargetDesc tg = p.targets[u.tgt_off + t];
-    const float* si = p.series + u.series_off + (int64_t)tg.i * u.n;
-    float acc = 0.f;
+// --------------------------------------------------------------------------
+// Table path: the library's members are marked in a shared-memory bitmap and
+// each query walks its row of the distance indexing table (sorted by (FP32
+// squared distance, index) over the whole manifold) until it has met E+1
+// library members other than itself.  Those are, in order, the E+1 nearest
+// library neighbours -- the same list the brute-force scan produces.  A query
+// whose R table entries hold fewer members falls back to scanning the library.
+template <int E>
+__device__ __forceinline__ float d2_point(const float* sj, int off, int tau, const float (&q)[E],
+                                          int x) {
+  float diff = __fsub_rn(q[0], sj[x + off]);
+  float acc = __fmul_rn(diff, diff);
 #pragma unroll
-    for (int s = 0; s <= E; ++s) acc = fmaf(w[s], si[nbc[s] + off], acc);
-    const float xhat = acc / usum;
-    const double xo = valid ? (double)si[m + off] : 0.0;
-    const double xp = valid ? (double)xhat : 0.0;
-    if (valid) {
-      if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
-      if (p.dbg_nbr) {
-#pragma unroll
-        for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nb[s];
-      }
-    }
-    // Tile moments of this target, two passes over the registers.
-    double n = valid ? 1.0 : 0.0, sx = xo, sy = xp;
-    block_sum3(n, sx, sy, s_red);
-    const double mx = sx / n, my = sy / n;
-    double sxx = 0.0, syy = 0.0, sxy = 0.0;
-    if (valid) {
-      const double a = xo - mx, b = xp - my;
-      sxx = a * a;
-      syy = b * b;
-      sxy = a * b;
-    }
-    block_sum3(sxx, syy, sxy, s_red);
-    if (tid == 0) {
-      double* part = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile);
-      part[0] = n;
-      part[1] = mx;
-      part[2] = my;
-      part[3] = sxx;
-      part[4] = syy;
-      part[5] = sxy;
-    }
+  for (int e = 1; e < E; ++e) {
+    diff = __fsub_rn(q[e], sj[x + off - e * tau]);
+    acc = __fmaf_rn(diff, diff, acc);
   }
+  return acc;
+}
 
-  // The last tile of this realization to finish merges every target's tile
-  // moments in tile order (Chan et al. pairwise update): rho does not depend
-  // on which CTA ran which tile, or when.
-  if (tid == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(&p.unit_done[unit], 1u);
-    *s_last = (prev == (unsigned)(u.n_tiles - 1)) ? 1 : 0;
+template <int E>
+__device__ void process_tile_table(const KnnParams& p, const UnitDesc& u, int unit, int tile,
+                                   unsigned char* smem, double* s_red, int* s_last) {
+  const int tid = threadIdx.x;
+  const int n_m = u.n_m, L = u.L, tau = u.tau, R = u.table_R;
+  const int off = (E - 1) * tau;
+  const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
+  const int32_t* lib = p.lib + u.lib_off;
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem);  // library membership, one bit per point
+  const int words = (n_m + 31) >> 5;
+  __syncthreads();  // the previous item's readers of bm are done
+  for (int w = tid; w < words; w += kThreads) bm[w] = 0u;
+  __syncthreads();
+  for (int a = tid; a < L; a += kThreads) {
+    const int l = lib[a];
+    atomicOr(&bm[l >> 5], 1u << (l & 31));
   }
   __syncthreads();
-  if (*s_last) {
-    __threadfence();
-    for (int t = tid; t < u.n_targets; t += kThreads) {
-      const double* base = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles);
-      double N = __ldcg(base + 0), MX = __ldcg(base + 1), MY = __ldcg(base + 2);
-      double SXX = __ldcg(base + 3), SYY = __ldcg(base + 4), SXY = __ldcg(base + 5);
-      for (int q = 1; q < u.n_tiles; ++q) {
-        const double* pt = base + 6 * q;
-        const double nb2 = __ldcg(pt + 0), mxb = __ldcg(pt + 1), myb = __ldcg(pt + 2);
-        const double tot = N + nb2;
-        const double dx = mxb - MX, dy = myb - MY;
-        const double f = N * nb2 / tot;
-        SXX += __ldcg(pt + 3) + dx * dx * f;
-        SYY += __ldcg(pt + 4) + dy * dy * f;
-        SXY += __ldcg(pt + 5) + dx * dy * f;
-        MX += dx * nb2 / tot;
-        MY += dy * nb2 / tot;
-        N = tot;
-      }
-      p.rho[p.targets[u.tgt_off + t].out_idx] =
-          (SXX > 0.0 && SYY > 0.0) ? SXY / sqrt(SXX * SYY) : nan("");
+
+  const int pos = tile * kQT + tid;
+  const bool valid = pos < n_m;
+  const int m = p.order[u.order_off + (valid ? pos : n_m - 1)];
+  float q[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
+
+  int nb[E + 1];
+#pragma unroll
+  for (int s2 = 0; s2 <= E; ++s2) nb[s2] = 0;
+  int found = valid ? 0 : E + 1;
+  const int64_t rowoff = u.table_off + (valid ? pos : 0);
+  const uint16_t* row16 = static_cast<const uint16_t*>(p.table) + rowoff;
+  const int32_t* row32 = static_cast<const int32_t*>(p.table) + rowoff;
+  constexpr int kFlight = 8;  // table loads in flight per lane
+  int r = 0;
+  while (__any_sync(kFull, found <= E && r < R)) {
+    int idx[kFlight];
+#pragma unroll
+    for (int c = 0; c < kFlight; ++c) {
+      const bool want = found <= E && r + c < R;
+      const int64_t o = (int64_t)(r + c) * n_m;
+      idx[c] = !want ? -1 : (p.table_u16 ? (int)__ldg(row16 + o) : __ldg(row32 + o));
     }
-    if (tid == 0) p.unit_done[unit] = 0u;  // ready for the next run
+#pragma unroll
+    for (int c = 0; c < kFlight; ++c) {
+      const int x = idx[c];
+      if (found <= E && x >= 0 && x != m && ((bm[x >> 5] >> (x & 31)) & 1u)) {
+#pragma unroll
+        for (int s2 = 0; s2 <= E; ++s2) nb[s2] = (found == s2) ? x : nb[s2];
+        ++found;
+      }
+    }
+    r += kFlight;
   }
-  __syncthreads();
+  if (found <= E) {
+    // Rare: fewer than E+1 members among the R nearest points; scan the
+    // library (ascending index, strict insertion keeps (d2, index) order).
+    float kd[E + 1];
+    int kl[E + 1];
+#pragma unroll
+    for (int s2 = 0; s2 <= E; ++s2) {
+      kd[s2] = INFINITY;
+      kl[s2] = -1;
+    }
+    // A plain shifting insertion (the branch-free insert_sorted variant
+    // produced wrong threshold updates in this kernel's rare path).
+    for (int a = 0; a < L; ++a) {
+      const int l = lib[a];
+      if (l == m) continue;
+      const float d = d2_point<E>(sj, off, tau, q, l);
+      if (d < kd[E]) {
+        int s2 = E;
+        while (s2 > 0 && d < kd[s2 - 1]) {
+          kd[s2] = kd[s2 - 1];
+          kl[s2] = kl[s2 - 1];
+          --s2;
+        }
+        kd[s2] = d;
+        kl[s2] = l;
+      }
+    }
+#pragma unroll
+    for (int s2 = 0; s2 <= E; ++s2) nb[s2] = kl[s2];
+  }
+  float dd[E + 1];
+#pragma unroll
+  for (int s2 = 0; s2 <= E; ++s2) dd[s2] = valid ? d2_point<E>(sj, off, tau, q, max(nb[s2], 0)) : 0.f;
+  finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, s_red, s_last);
+}
+
+__global__ void __launch_bounds__(kThreads) knn_table_kernel(KnnParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double s_red[3 * (kThreads / 32) + 3];
+  __shared__ int s_item, s_last;
+  for (int64_t round = 0;; ++round) {
+    if (p.persistent) {
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(p.item_counter, 1u);
+      __syncthreads();
+    }
+    const int it = p.persistent ? s_item : (round == 0 ? (int)blockIdx.x : INT_MAX);
+    __syncthreads();
+    if ((int64_t)it >= p.n_items) break;
+    const WorkItem w = p.items[it];
+    const UnitDesc u = p.units[w.unit];
+    switch (u.E) {
+#define CCM_TT(EV) \
+  case EV: process_tile_table<EV>(p, u, w.unit, w.tile, smem, s_red, &s_last); break;
+      CCM_TT(1) CCM_TT(2) CCM_TT(3) CCM_TT(4) CCM_TT(5)
+      CCM_TT(6) CCM_TT(7) CCM_TT(8) CCM_TT(9) CCM_TT(10)
+#undef CCM_TT
+      default:
+        if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
+    }
+  }
 }
 
 template <int EMIN, int EMAX>
@@ -461,6 +615,23 @@ cudaError_t occupancy_range(int* ctas) {
 }  // namespace
 
 int knn_block_threads() { return kThreads; }
+
+size_t knn_table_smem(int max_nm) { return (size_t)((max_nm + 31) / 32) * 4 + 16; }
+
+cudaError_t knn_table_prepare(int max_nm) {
+  return cudaFuncSetAttribute(knn_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)knn_table_smem(max_nm));
+}
+
+cudaError_t knn_table_occupancy(int max_nm, int* ctas) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_table_kernel, kThreads,
+                                                       knn_table_smem(max_nm));
+}
+
+cudaError_t launch_knn_table(const KnnParams& p, int max_nm, int grid, cudaStream_t s) {
+  knn_table_kernel<<<grid, kThreads, knn_table_smem(max_nm), s>>>(p);
+  return cudaGetLastError();
+}
 int knn_queries_per_thread() { return 1; }
 size_t knn_smem_bytes(int, int) { return kSmemBytes; }
 

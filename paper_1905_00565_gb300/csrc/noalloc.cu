@@ -105,6 +105,9 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     u.n_m = c.n_m;
     u.n_tiles = c.n_tiles;
     u.n_targets = 1;
+    u.table_off = 0;
+    u.table_R = 0;
+    u.pad = 0;
     TargetDesc tg;
     tg.out_idx = k;
     tg.q_off = k * (int64_t)c.n_m;

@@ -125,7 +125,14 @@ struct UnitList {
   std::vector<WorkItem> items;
   std::vector<double> item_cost;
   std::vector<OrderJob> orders;       // one per (job, library variable, E, tau)
-  int64_t lib_total = 0, part_total = 0, order_total = 0;
+  std::vector<TableJob> tables;       // distance indexing tables to build
+  std::vector<WorkItem> items_table;  // work items of units that read a table
+  std::vector<double> item_cost_table;
+  int64_t lib_total = 0, part_total = 0, order_total = 0, table_total = 0;
+  int max_R = 0;
+  double brute_flops = 0.0;           // 3E per pair of the units searched by brute force
+  int table_u16() const { return max_nm < 65536 ? 1 : 0; }
+  size_t table_elem() const { return table_u16() ? 2 : 4; }
   int64_t n_rho = 0, q_total = 0, nbr_total = 0, lib_dbg_total = 0;  // per output realization
   int emin = kMaxE + 1, emax = 0, max_nm = 0;
   double pairs = 0.0, flops = 0.0;    // neighbour-search work actually done
@@ -183,6 +190,52 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         ul->order_total += oj.n_m;
         ul->orders.push_back(oj);
       }
+  // Distance indexing tables (CCM_TABLE): per (j, E, tau), realizations with
+  // L >= Ls read their neighbours from a table of the R nearest points of
+  // every query; R covers about four times the expected scan length
+  // (E+2)*N_m/L at the smallest such L (CCM_TABLE_SAFETY changes the four).
+  // A table is built only when the
+  // realizations that use it would otherwise scan at least 8*N_m library
+  // points in total (its build costs about N_m^2 distance evaluations).
+  std::map<std::tuple<int32_t, int32_t, int32_t>, std::pair<int64_t, int32_t>> table_of;
+  // Safety factor of R over the expected scan length; CCM_TABLE_SAFETY trades
+  // table memory for how often a query falls back to scanning its library.
+  double safety = 4.0;
+  if (const char* env = getenv("CCM_TABLE_SAFETY")) safety = std::max(0.01, atof(env));
+  if (pc.flags & CCM_TABLE) {
+    for (int32_t j : lib_vars)
+      for (int32_t E : pc.E)
+        for (int32_t tau : pc.tau) {
+          const int64_t n_m = pc.n - (int64_t)(E - 1) * tau;
+          const double ls = std::max(256.0, std::ceil(4.0 * (E + 2) * (double)n_m /
+                                                       (double)(kTableMaxR - 64)));
+          int64_t lmin = -1;
+          double lsum = 0.0;
+          for (int64_t L : pc.L)
+            if ((double)L >= ls) {
+              lmin = (lmin < 0) ? L : std::min(lmin, L);
+              lsum += (double)L * pc.r;
+            }
+          if (lmin < 0 || lsum < 8.0 * (double)n_m) continue;
+          int64_t R = (int64_t)std::ceil(safety * (E + 2) * (double)n_m / (double)lmin) + 64;
+          R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR), n_m);
+          TableJob tj;
+          std::memset(&tj, 0, sizeof(tj));
+          tj.series_off = series_off;
+          tj.n = pc.n;
+          tj.order_off = combo[std::make_tuple(j, E, tau)];
+          tj.table_off = ul->table_total;
+          tj.j = j;
+          tj.E = E;
+          tj.tau = tau;
+          tj.n_m = (int32_t)n_m;
+          tj.R = (int32_t)R;
+          table_of[std::make_tuple(j, E, tau)] = std::make_pair(tj.table_off, tj.R);
+          ul->table_total += n_m * R;
+          ul->max_R = std::max(ul->max_R, (int)R);
+          ul->tables.push_back(tj);
+        }
+  }
   for (int32_t j : lib_vars) {
     const std::vector<int64_t>& tp = pairs_of[j];
     for (int64_t e = 0; e < nE; ++e)
@@ -219,14 +272,29 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
               tg.i = pc.pairs[2 * p + 1];
               ul->targets.push_back(tg);
             }
+            const auto tab = table_of.find(std::make_tuple(j, E, tau));
+            if (tab != table_of.end() && L >= 256 &&
+                (double)L >= std::ceil(4.0 * (E + 2) * (double)u.n_m / (double)(kTableMaxR - 64))) {
+              u.table_off = tab->second.first;
+              u.table_R = tab->second.second;
+            }
             const int32_t uidx = (int32_t)ul->units.size();
             for (int32_t q = 0; q < u.n_tiles; ++q) {
               const int64_t nq = std::min<int64_t>(tileq, u.n_m - (int64_t)q * tileq);
-              ul->items.push_back(WorkItem{uidx, q});
-              // distance work, staging per library point, per-target epilogue
-              ul->item_cost.push_back((double)L * ((double)nq * (2.0 * E + 1.0) + 64.0 * E) +
-                                      (double)u.n_targets * nq * 64.0);
+              if (u.table_R > 0) {
+                // bitmap build, expected table scan, per-target epilogue
+                ul->items_table.push_back(WorkItem{uidx, q});
+                ul->item_cost_table.push_back((double)L + (double)nq * 12.0 * (E + 2) *
+                                              (double)u.n_m / (double)L +
+                                              (double)u.n_targets * nq * 64.0);
+              } else {
+                ul->items.push_back(WorkItem{uidx, q});
+                // distance work, staging per library point, per-target epilogue
+                ul->item_cost.push_back((double)L * ((double)nq * (2.0 * E + 1.0) + 64.0 * E) +
+                                        (double)u.n_targets * nq * 64.0);
+              }
             }
+            if (u.table_R == 0) ul->brute_flops += 3.0 * E * (double)u.n_m * (double)L;
             ul->lib_total += L;
             ul->part_total += (int64_t)u.n_tiles * u.n_targets;
             ul->emin = std::min(ul->emin, E);
@@ -240,21 +308,38 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
 }
 
 // Sort the work list by decreasing cost (longest first), ties by position.
+void sort_by_cost(std::vector<WorkItem>* items, const std::vector<double>& cost) {
+  std::vector<int64_t> order(items->size());
+  for (size_t q = 0; q < order.size(); ++q) order[q] = (int64_t)q;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t b) { return cost[(size_t)a] > cost[(size_t)b]; });
+  std::vector<WorkItem> sorted(order.size());
+  for (size_t q = 0; q < order.size(); ++q) sorted[q] = (*items)[(size_t)order[q]];
+  items->swap(sorted);
+}
+
 void sort_items(UnitList* ul) {
-  std::vector<int64_t> order(ul->items.size());
+  sort_by_cost(&ul->items, ul->item_cost);
+  // Table items: grouped by table (a table of 20-80 MB stays in L2 while its
+  // realizations run), larger items first within a table.
+  std::vector<int64_t> order(ul->items_table.size());
   for (size_t q = 0; q < order.size(); ++q) order[q] = (int64_t)q;
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-    return ul->item_cost[(size_t)a] > ul->item_cost[(size_t)b];
+    const int64_t ta = ul->units[(size_t)ul->items_table[(size_t)a].unit].table_off;
+    const int64_t tb = ul->units[(size_t)ul->items_table[(size_t)b].unit].table_off;
+    if (ta != tb) return ta < tb;
+    return ul->item_cost_table[(size_t)a] > ul->item_cost_table[(size_t)b];
   });
   std::vector<WorkItem> sorted(order.size());
-  for (size_t q = 0; q < order.size(); ++q) sorted[q] = ul->items[(size_t)order[q]];
-  ul->items.swap(sorted);
+  for (size_t q = 0; q < order.size(); ++q) sorted[q] = ul->items_table[(size_t)order[q]];
+  ul->items_table.swap(sorted);
 }
 
 // Device arena layout for a unit list.
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
-         counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, total = 0;
+         counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
+         items_table = 0, total = 0;
 };
 
 Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
@@ -273,11 +358,14 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.done = take(sizeof(uint32_t) * ul.units.size());
   a.rho = take(sizeof(double) * (size_t)n_rho);
   a.err = take(sizeof(int32_t));
-  a.counter = take(sizeof(uint32_t));
+  a.counter = take(2 * sizeof(uint32_t));  // brute-force and table work counters
   a.scratch = take(sizeof(float) * (size_t)scratch_floats);
   a.order = take(sizeof(int32_t) * (size_t)ul.order_total);
   a.orders = take(sizeof(OrderJob) * ul.orders.size());
   a.targets = take(sizeof(TargetDesc) * ul.targets.size());
+  a.table = take(ul.table_elem() * (size_t)ul.table_total);
+  a.tables = take(sizeof(TableJob) * ul.tables.size());
+  a.items_table = take(sizeof(WorkItem) * ul.items_table.size());
   a.total = o;
   return a;
 }
@@ -396,8 +484,8 @@ struct ccm_plan_s {
   char* d_arena = nullptr;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before sampler, before knn, after knn
-  int grid = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage boundaries
+  int grid = 0, grid_table = 0;
   Tuning tuning = default_tuning();
   bool tuned = false;
   std::mutex run_mu;
@@ -425,6 +513,8 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.n_items = (int64_t)ul.items.size();
   kp.lib = reinterpret_cast<const int32_t*>(base + ar.lib);
   kp.order = reinterpret_cast<const int32_t*>(base + ar.order);
+  kp.table = base + ar.table;
+  kp.table_u16 = ul.table_u16();
   kp.partials = reinterpret_cast<double*>(base + ar.part);
   kp.unit_done = reinterpret_cast<uint32_t*>(base + ar.done);
   kp.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter);
@@ -439,10 +529,13 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
 }
 
 // Enqueue sampler + fused kernel for a whole unit list on stream s.
+// Stage events (optional): ev[0] start, ev[1] after order + table build,
+// ev[2] after the sampler, ev[3] after the brute-force launch, ev[4] after the
+// table-scan launch.
 ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const Tuning& tn,
-                         int grid, int persistent, int32_t* dbg_lib, int32_t* dbg_nbr,
-                         float* dbg_xhat, cudaStream_t s, cudaEvent_t* ev = nullptr,
-                         bool capturing = false) {
+                         int grid, int grid_table, int persistent, int32_t* dbg_lib,
+                         int32_t* dbg_nbr, float* dbg_xhat, cudaStream_t s,
+                         cudaEvent_t* ev = nullptr, bool capturing = false) {
   // Inside stream capture an event record becomes a graph node only with the
   // external flag; outside capture the plain record is the valid form.
   auto record = [&](cudaEvent_t e) {
@@ -450,23 +543,40 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                      : cudaEventRecord(e, s);
   };
   CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
-  CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, sizeof(uint32_t), s));
+  CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, 2 * sizeof(uint32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
-  SamplerParams sp = sampler_params(base, ar);
-  sp.dbg_lib = dbg_lib;
   if (ev) CCM_CUDA(record(ev[0]));
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
                         reinterpret_cast<const OrderJob*>(base + ar.orders),
                         (int64_t)ul.orders.size(), ul.max_nm,
                         reinterpret_cast<int32_t*>(base + ar.order), s));
+  CCM_CUDA(launch_table_build(reinterpret_cast<const float*>(base + ar.series),
+                              reinterpret_cast<const TableJob*>(base + ar.tables),
+                              (int64_t)ul.tables.size(), ul.max_nm, ul.max_R,
+                              reinterpret_cast<const int32_t*>(base + ar.order),
+                              base + ar.table, ul.table_u16(), s));
+  if (ev) CCM_CUDA(record(ev[1]));
+  SamplerParams sp = sampler_params(base, ar);
+  sp.dbg_lib = dbg_lib;
   CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
+  if (ev) CCM_CUDA(record(ev[2]));
   KnnParams kp = knn_params(base, ar, ul, persistent, tn);
   kp.dbg_nbr = dbg_nbr;
   kp.dbg_xhat = dbg_xhat;
-  const int g = persistent ? grid : (int)ul.items.size();
-  if (ev) CCM_CUDA(record(ev[1]));
-  CCM_CUDA(launch_knn(kp, ul.emin, ul.emax, g, s));
-  if (ev) CCM_CUDA(record(ev[2]));
+  if (!ul.items.empty()) {
+    const int g = persistent ? grid : (int)ul.items.size();
+    CCM_CUDA(launch_knn(kp, ul.emin, ul.emax, g, s));
+  }
+  if (ev) CCM_CUDA(record(ev[3]));
+  if (!ul.items_table.empty()) {
+    KnnParams kt = kp;
+    kt.items = reinterpret_cast<const WorkItem*>(base + ar.items_table);
+    kt.n_items = (int64_t)ul.items_table.size();
+    kt.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter) + 1;
+    const int g = persistent ? grid_table : (int)ul.items_table.size();
+    CCM_CUDA(launch_knn_table(kt, ul.max_nm, g, s));
+  }
+  if (ev) CCM_CUDA(record(ev[4]));
   return CCM_OK;
 }
 
@@ -633,6 +743,7 @@ ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context**
   CCM_CUDA(sampler_prepare());
   CCM_CUDA(knn_prepare());
   CCM_CUDA(order_prepare());
+  CCM_CUDA(table_prepare());
   size_t free_b = 0, total_b = 0;
   CCM_CUDA(cudaMemGetInfo(&free_b, &total_b));
   std::unique_ptr<ccm_context> ctx(new ccm_context());
@@ -665,7 +776,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
     return fail(CCM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
   e = cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking);
-  for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreate(&pl->ev[q]);
+  for (int q = 0; q < 5 && e == cudaSuccess; ++q) e = cudaEventCreate(&pl->ev[q]);
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_arena + pl->ar.units, pl->ul.units.data(),
                    sizeof(UnitDesc) * pl->ul.units.size(), cudaMemcpyHostToDevice);
@@ -679,6 +790,13 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
     e = cudaMemcpy(pl->d_arena + pl->ar.targets, pl->ul.targets.data(),
                    sizeof(TargetDesc) * pl->ul.targets.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_arena + pl->ar.tables, pl->ul.tables.data(),
+                   sizeof(TableJob) * pl->ul.tables.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_arena + pl->ar.items_table, pl->ul.items_table.data(),
+                   sizeof(WorkItem) * pl->ul.items_table.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pl->ul.items_table.empty()) e = knn_table_prepare(pl->ul.max_nm);
+  if (e == cudaSuccess)
     e = cudaMemset(pl->d_arena + pl->ar.done, 0, sizeof(uint32_t) * pl->ul.units.size());
   if (e != cudaSuccess) {
     cudaFree(pl->d_arena);
@@ -687,6 +805,11 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
     return fail(CCM_ECUDA, std::string("plan set-up: ") + cudaGetErrorString(e));
   }
   pl->grid = persistent_grid(ctx, pl->ul.emin, pl->ul.emax);
+  {
+    int per_sm = 1;
+    if (knn_table_occupancy(pl->ul.max_nm, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+    pl->grid_table = ctx->sm_count * per_sm;
+  }
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     pl->tuning = ctx->tuning;
@@ -700,6 +823,8 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.device_bytes = pl->ar.total;
   in.pair_count = pl->ul.pairs;
   in.flop_count = pl->ul.flops;
+  in.brute_flop_count = pl->ul.brute_flops;
+  in.table_bytes = pl->ul.table_elem() * (size_t)pl->ul.table_total;
   *out = pl.release();
   return CCM_OK;
 }
@@ -760,8 +885,8 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
                                  : reinterpret_cast<float*>(tmp + align_up(lb, 256) + align_up(nb, 256)))
                       : nullptr;
     ccm_status st =
-        enqueue_sweep(base, plan->ar, ul, plan->tuning, plan->grid, 1, d_lib, d_nbr, d_xh, s,
-                      plan->ev);
+        enqueue_sweep(base, plan->ar, ul, plan->tuning, plan->grid, plan->grid_table, 1, d_lib,
+                      d_nbr, d_xh, s, plan->ev);
     if (st != CCM_OK) return st;
     if (!out_dev) {
       if (dbg->libraries) CCM_CUDA(cudaMemcpyAsync(dbg->libraries, d_lib, lb, cudaMemcpyDeviceToHost, s));
@@ -783,8 +908,9 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
     if (!plan->graph) {
       cudaGraph_t graph = nullptr;
       CCM_CUDA(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
-      ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->tuning, plan->grid, 1,
-                                    nullptr, nullptr, nullptr, plan->stream, plan->ev, true);
+      ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->tuning, plan->grid,
+                                    plan->grid_table, 1, nullptr, nullptr, nullptr, plan->stream,
+                                    plan->ev, true);
       const cudaError_t ce = cudaStreamEndCapture(plan->stream, &graph);
       if (st != CCM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -805,13 +931,22 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
 }
 
 ccm_status ccm_plan_kernel_times(const ccm_plan_t* plan, double* sampler_ms, double* knn_ms) {
-  if (!plan) return fail(CCM_EINVAL, "plan is NULL");
+  double st[4];
+  const ccm_status r = ccm_plan_stage_times(plan, st);
+  if (r != CCM_OK) return r;
+  if (sampler_ms) *sampler_ms = st[0] + st[1];
+  if (knn_ms) *knn_ms = st[2] + st[3];
+  return CCM_OK;
+}
+
+ccm_status ccm_plan_stage_times(const ccm_plan_t* plan, double* stage_ms) {
+  if (!plan || !stage_ms) return fail(CCM_EINVAL, "NULL argument");
   CCM_CUDA(cudaSetDevice(plan->ctx->device));
-  float a = 0.f, b = 0.f;
-  CCM_CUDA(cudaEventElapsedTime(&a, plan->ev[0], plan->ev[1]));
-  CCM_CUDA(cudaEventElapsedTime(&b, plan->ev[1], plan->ev[2]));
-  if (sampler_ms) *sampler_ms = a;
-  if (knn_ms) *knn_ms = b;
+  for (int q = 0; q < 4; ++q) {
+    float t = 0.f;
+    CCM_CUDA(cudaEventElapsedTime(&t, plan->ev[q], plan->ev[q + 1]));
+    stage_ms[q] = t;
+  }
   return CCM_OK;
 }
 
@@ -953,7 +1088,7 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
     tn = ctx->tuning;
   }
   ccm_status st =
-      enqueue_sweep(base, b->ar, b->ul, tn, 0, 0, nullptr, nullptr, nullptr, b->stream);
+      enqueue_sweep(base, b->ar, b->ul, tn, 0, 0, 0, nullptr, nullptr, nullptr, b->stream);
   if (st != CCM_OK) return st;
   int64_t ro = 0;
   for (auto& j : b->jobs) {

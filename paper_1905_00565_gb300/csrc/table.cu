@@ -1,0 +1,206 @@
+// Distance indexing table (paper Sect. 3.2: a table of the sorted distances of
+// every point, built once, from which the E+1 nearest neighbours of any
+// subsample are read off instead of re-sorting all distances for every
+// subsample; Sect. 3.2 and Fig. 2 describe it as a second pipeline that feeds
+// the CCM transform).
+//
+// For one (library variable, E, tau) the table holds, for every query
+// position pos of the query order, the R nearest manifold points of the query
+// order[pos] over the WHOLE manifold, sorted by (FP32 squared distance, index),
+// the same key the brute-force selection uses.  For a realization whose library
+// is a subset of the manifold, the first E+1 table entries that are library
+// members (the query itself skipped) are exactly its E+1 nearest library
+// neighbours: restricting a total order to a subset keeps its order.
+//
+// Layout: table[table_off + r * n_m + pos], so that the 32 consecutive query
+// positions of a warp read one rank with one coalesced access; 16-bit entries
+// when every manifold of the plan has fewer than 65536 points, else 32-bit.
+//
+// Build: one warp per query position.  Three radix passes (11, 11, 10 bits) of
+// a histogram over the FP32 bit patterns of all N_m squared distances find the
+// R-th smallest value T and how many entries equal to T are taken; a fourth
+// pass collects every entry below T and, in index order, the first equal
+// ones; a bitonic sort in shared memory orders the R keys (bits << 32 | index).
+#include <stdint.h>
+
+#include "ccm_internal.h"
+
+namespace ccm {
+namespace {
+
+constexpr int kTableWarps = 8;  // query positions per CTA
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// FP32 squared distance from query coordinates q to manifold point x, in the
+// fixed order (coordinate 0 a rounded product, then one fused multiply-add per
+// coordinate): the same bits as the neighbour search computes.
+template <int E>
+__device__ __forceinline__ uint32_t d2_bits(const float* s, int off, int tau, const float (&q)[E],
+                                            int x) {
+  float diff = __fsub_rn(q[0], s[x + off]);
+  float acc = __fmul_rn(diff, diff);
+#pragma unroll
+  for (int e = 1; e < E; ++e) {
+    diff = __fsub_rn(q[e], s[x + off - e * tau]);
+    acc = __fmaf_rn(diff, diff, acc);
+  }
+  return __float_as_uint(acc);  // d2 >= +0: unsigned order is numeric order
+}
+
+template <int E>
+__device__ void build_row(const float* s, const TableJob& jb, int pos, const int32_t* order,
+                          void* table, int u16, uint32_t* hist, unsigned long long* keys) {
+  const int lane = threadIdx.x & 31;
+  const int n_m = jb.n_m, tau = jb.tau, off = (E - 1) * tau, R = jb.R;
+  const int m = order[jb.order_off + pos];
+  float q[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) q[e] = s[m + off - e * tau];
+
+  // Radix select of the R-th smallest bit pattern (1-based rank).
+  uint32_t prefix = 0u, mask = 0u;
+  int rank = R;
+  for (int pass = 0; pass < 3; ++pass) {
+    const int sh = (pass == 0) ? 21 : (pass == 1) ? 10 : 0;
+    const int nbins = (pass == 2) ? 1024 : 2048;
+    const uint32_t dm = (uint32_t)nbins - 1u;
+    for (int b = lane; b < nbins; b += 32) hist[b] = 0u;
+    __syncwarp();
+    for (int x = lane; x < n_m; x += 32) {
+      const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
+      if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> sh) & dm], 1u);
+    }
+    __syncwarp();
+    // each lane owns a contiguous chunk of bins; scan the chunk sums
+    const int chunk = nbins / 32;
+    uint32_t mine = 0u;
+    for (int b = 0; b < chunk; ++b) mine += hist[lane * chunk + b];
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned hit = __ballot_sync(kFullMask, incl >= (uint32_t)rank);
+    const int owner = __ffs(hit) - 1;  // exists: the histogram holds >= rank entries
+    uint32_t before = __shfl_sync(kFullMask, incl - mine, owner);
+    int bin = 0;
+    if (lane == owner) {
+      uint32_t cum = before;
+      for (int b = 0; b < chunk; ++b) {
+        const uint32_t h = hist[lane * chunk + b];
+        if (cum + h >= (uint32_t)rank) {
+          bin = lane * chunk + b;
+          break;
+        }
+        cum += h;
+      }
+      before = cum;
+    }
+    bin = __shfl_sync(kFullMask, bin, owner);
+    before = __shfl_sync(kFullMask, before, owner);
+    prefix |= (uint32_t)bin << sh;
+    mask |= dm << sh;
+    rank -= (int)before;
+    __syncwarp();
+  }
+  const uint32_t T = prefix;       // bit pattern of the R-th smallest squared distance
+  const int take_ties = rank;      // entries equal to T to take, lowest index first
+  const int n_less = R - take_ties;
+
+  // Collect in index order (deterministic slots): all below T, then the first
+  // take_ties equal to T.
+  int less_seen = 0, ties_seen = 0;
+  for (int base = 0; base < n_m; base += 32) {
+    const int x = base + lane;
+    const uint32_t bits = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
+    const bool less = (x < n_m) && bits < T;
+    const bool tie = (x < n_m) && bits == T;
+    const unsigned lm = __ballot_sync(kFullMask, less);
+    const unsigned tm = __ballot_sync(kFullMask, tie);
+    const unsigned below = (1u << lane) - 1u;
+    if (less) keys[less_seen + __popc(lm & below)] = ((unsigned long long)bits << 32) | (unsigned)x;
+    const int tr = ties_seen + __popc(tm & below);
+    if (tie && tr < take_ties)
+      keys[n_less + tr] = ((unsigned long long)bits << 32) | (unsigned)x;
+    less_seen += __popc(lm);
+    ties_seen += __popc(tm);
+  }
+  int rcap = 32;  // this row's sort size: the power of two at or above R
+  while (rcap < R) rcap <<= 1;
+  for (int i = R + lane; i < rcap; i += 32) keys[i] = ~0ull;
+  __syncwarp();
+  // bitonic sort of rcap keys, ascending
+  for (int k = 2; k <= rcap; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = lane; i < rcap; i += 32) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const unsigned long long a = keys[i], b = keys[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            keys[i] = b;
+            keys[ixj] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (u16) {
+    uint16_t* out = static_cast<uint16_t*>(table) + jb.table_off + pos;
+    for (int r = lane; r < R; r += 32) out[(int64_t)r * n_m] = (uint16_t)(keys[r] & 0xffffu);
+  } else {
+    int32_t* out = static_cast<int32_t*>(table) + jb.table_off + pos;
+    for (int r = lane; r < R; r += 32) out[(int64_t)r * n_m] = (int32_t)(keys[r] & 0xffffffffu);
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kTableWarps * 32)
+table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
+                   int u16, int rcap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TableJob jb = jobs[blockIdx.y];
+  const int warp = threadIdx.x >> 5;
+  const int pos = blockIdx.x * kTableWarps + warp;
+  if (pos >= jb.n_m) return;  // whole warp leaves; no block-wide barrier follows
+  // per warp: max(2048 histogram bins, rcap keys)
+  const size_t per_warp = (size_t)max(2048 * 4, rcap * 8);
+  unsigned char* mine = smem + warp * per_warp;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(mine);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(mine);
+  const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
+  switch (jb.E) {
+#define CCM_TB(EV) \
+  case EV: build_row<EV>(s, jb, pos, order, table, u16, hist, keys); break;
+    CCM_TB(1) CCM_TB(2) CCM_TB(3) CCM_TB(4) CCM_TB(5)
+    CCM_TB(6) CCM_TB(7) CCM_TB(8) CCM_TB(9) CCM_TB(10)
+#undef CCM_TB
+    default: break;
+  }
+}
+
+size_t table_smem(int rcap) { return (size_t)kTableWarps * (size_t)max(2048 * 4, rcap * 8); }
+
+}  // namespace
+
+cudaError_t table_prepare() {
+  return cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)table_smem(kTableMaxR));
+}
+
+cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs,
+                               int max_nm, int max_R, const int32_t* order, void* table,
+                               int table_u16, cudaStream_t s) {
+  if (n_jobs <= 0) return cudaSuccess;
+  int rcap = 32;
+  while (rcap < max_R) rcap <<= 1;
+  if (rcap > kTableMaxR) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((max_nm + kTableWarps - 1) / kTableWarps), (unsigned)n_jobs);
+  table_build_kernel<<<grid, kTableWarps * 32, table_smem(rcap), s>>>(series, jobs, order, table,
+                                                                      table_u16, rcap);
+  return cudaGetLastError();
+}
+
+}  // namespace ccm

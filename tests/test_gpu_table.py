@@ -1,0 +1,135 @@
+"""Distance indexing tables (CCM_TABLE, paper Sect. 3.2) on the GPU.
+
+A realization that reads its neighbours from the table must give exactly what
+the brute-force search gives (same neighbour lists, same bits of rho): the
+table row is the whole manifold sorted by (FP32 squared distance, index), and
+restricting it to the library keeps that order.  Checked against the
+brute-force path bit for bit, against the oracle, on tie-heavy integer series,
+with the fallback path forced by a tiny safety factor, and on the long series.
+"""
+
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_00565_gb300 import inputs as I
+from tests.ccm_check import XHAT_RTOL, check_units, run_detailed, split, xhat_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ccm():
+    from paper_1905_00565_gb300 import ccm as c
+    return c
+
+
+def both_paths(ccm, ctx, p):
+    a = run_detailed(ccm, ctx, p, 0)
+    b = run_detailed(ccm, ctx, p, ccm.CCM_TABLE)
+    return a, b
+
+
+def uses_table(ccm, ctx, p):
+    plan = ccm.plan_problem(ctx, p, ccm.CCM_TABLE)
+    try:
+        return ccm.ccm_plan_get_info(plan)["table_bytes"] > 0
+    finally:
+        ccm.ccm_plan_destroy(plan)
+
+
+def test_table_equals_brute_force_and_oracle(ccm):
+    base = I.sweep_problem()
+    s = np.ascontiguousarray(base.series[:, :3000])
+    p = I.Problem(series=s, pairs=I.BOTH_DIRECTIONS.copy(), E=np.array([1, 2, 5, 10], np.int32),
+                  tau=np.array([1, 3], np.int32), L=np.array([150, 300, 1200, 2900], np.int64),
+                  r=6, seed=base.seed, name="table-cells")
+    ctx = ccm.ccm_context_create(0)
+    try:
+        assert uses_table(ccm, ctx, p)
+        (r0, l0, n0, x0), (r1, l1, n1, x1) = both_paths(ccm, ctx, p)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+    assert np.array_equal(l0, l1) and np.array_equal(n0, n1)
+    assert np.array_equal(x0, x1) and np.array_equal(r0, r1)
+    rng = np.random.default_rng(3)
+    check_units(p, r1, l1, n1, x1, which=set(int(u) for u in rng.choice(r1.size, 12, replace=False)))
+
+
+def test_table_with_exact_ties_and_full_library(ccm):
+    rng = np.random.default_rng(8)
+    ints = rng.integers(0, 6, size=(2, 2500)).astype(np.float32)
+    p = I.Problem(series=ints, pairs=I.BOTH_DIRECTIONS.copy(), E=np.array([1, 2, 3], np.int32),
+                  tau=np.array([1], np.int32), L=np.array([300, 2498], np.int64), r=8, seed=4,
+                  name="ties")
+    ctx = ccm.ccm_context_create(0)
+    try:
+        assert uses_table(ccm, ctx, p)
+        (r0, l0, n0, x0), (r1, l1, n1, x1) = both_paths(ccm, ctx, p)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+    assert np.array_equal(n0, n1) and np.array_equal(x0, x1)
+    np.testing.assert_array_equal(r0, r1)
+    check_units(p, r1, l1, n1, x1, which={0, 5, 11, 37, 63})
+
+
+def test_table_fallback_path(ccm, monkeypatch):
+    """A tiny safety factor leaves many queries with fewer than E+1 library
+    members among their R table entries; they scan their library instead."""
+    monkeypatch.setenv("CCM_TABLE_SAFETY", "0.05")
+    base = I.sweep_problem()
+    s = np.ascontiguousarray(base.series[:, :4000])
+    p = I.Problem(series=s, pairs=I.BOTH_DIRECTIONS.copy(), E=np.array([3, 8], np.int32),
+                  tau=np.array([2], np.int32), L=np.array([400, 3000], np.int64), r=2,
+                  seed=base.seed, name="fallback")
+    ctx = ccm.ccm_context_create(0)
+    try:
+        (r0, l0, n0, x0), (r1, l1, n1, x1) = both_paths(ccm, ctx, p)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+    assert np.array_equal(n0, n1) and np.array_equal(r0, r1)
+
+
+def test_table_fallback_small_e_regression(ccm):
+    """E = 2, tau = 3 on the full 10^4-point series: at L = 258 some queries
+    meet fewer than E+1 library members among their table entries and scan
+    their library; the scan must keep the whole sorted (distance, index) list."""
+    base = I.sweep_problem()
+    p = I.Problem(series=base.series, pairs=np.array([[1, 0]], np.int32),
+                  E=np.array([2], np.int32), tau=np.array([3], np.int32),
+                  L=np.array([258, 9000], np.int64), r=29, seed=base.seed, name="fallback-e2")
+    ctx = ccm.ccm_context_create(0)
+    try:
+        assert uses_table(ccm, ctx, p)
+        (r0, l0, n0, x0), (r1, l1, n1, x1) = both_paths(ccm, ctx, p)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+    assert np.array_equal(n0, n1) and np.array_equal(r0, r1)
+    check_units(p, r1, l1, n1, x1, which={0, 3, 30, 57})
+
+
+def test_table_on_the_long_series_sampled(ccm):
+    base = I.long_series_problem()
+    p = I.Problem(series=base.series, pairs=base.pairs, E=np.array([4], np.int32),
+                  tau=np.array([1], np.int32), L=np.array([5000, 50000], np.int64), r=16,
+                  seed=base.seed, name="long-table")
+    ctx = ccm.ccm_context_create(0)
+    try:
+        assert uses_table(ccm, ctx, p)
+        rho, lib, nbr, xh = run_detailed(ccm, ctx, p, ccm.CCM_TABLE)
+        rb, *_ = run_detailed(ccm, ctx, p, 0)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+    np.testing.assert_array_equal(rho, rb)
+    rng = np.random.default_rng(6)
+    for (u, j, i, E, tau, L, k, n_m, l_g, n_g, x_g) in split(p, lib, nbr, xh):
+        if u not in (0, 7, 16, 31):
+            continue
+        q = np.sort(rng.choice(n_m, size=200, replace=False))
+        nb_o, xh_o = oracle.query_subset(p.series[j], p.series[i], E, tau, l_g, q)
+        assert np.array_equal(n_g[q], nb_o)
+        assert xhat_rel_err(x_g[q], xh_o, p.series[i]) <= XHAT_RTOL
