@@ -9,7 +9,9 @@ Each wrapper names the step of the method it follows; the C++ file cites the
 paper's sections.  Neighbour selection is taken on FP32 squared distances by
 default (``select_fp64=False``), the precision the GPU kernel decides in, or on
 FP64 squared distances (``select_fp64=True``) to measure how often the FP32
-decision differs from the FP64 one.
+decision differs from the FP64 one.  Two options the paper does not discuss,
+off by default: an exclusion (Theiler) window ``theiler`` and a weight floor
+``weight_floor`` (see ``ccm_oracle.cpp``).
 """
 
 from __future__ import annotations
@@ -59,14 +61,15 @@ def _load():
             lib.oracle_library.restype = ctypes.c_int
             lib.oracle_neighbours.argtypes = [_F32P, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_int32, _I32P, ctypes.c_int64,
-                                              ctypes.c_int32, _I32P]
+                                              ctypes.c_int32, ctypes.c_int32, _I32P]
             lib.oracle_neighbours.restype = ctypes.c_int
             lib.oracle_predict.argtypes = [_F32P, _F32P, ctypes.c_int64, ctypes.c_int32,
-                                           ctypes.c_int32, _I32P, _F64P]
+                                           ctypes.c_int32, ctypes.c_double, _I32P, _F64P]
             lib.oracle_predict.restype = ctypes.c_int
             lib.oracle_query_subset.argtypes = [_F32P, _F32P, ctypes.c_int64, ctypes.c_int32,
                                                 ctypes.c_int32, _I32P, ctypes.c_int64, _I64P,
-                                                ctypes.c_int64, ctypes.c_int32, _I32P, _F64P]
+                                                ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_double, _I32P, _F64P]
             lib.oracle_query_subset.restype = ctypes.c_int
             lib.oracle_pearson.argtypes = [_F64P, _F64P, ctypes.c_int64]
             lib.oracle_pearson.restype = ctypes.c_double
@@ -76,13 +79,14 @@ def _load():
             lib.oracle_ccm_unit.argtypes = [_F32P, ctypes.c_int32, ctypes.c_int64,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
-                                            ctypes.c_uint64, ctypes.c_int32, _F64P, _I32P,
-                                            _I32P, _F64P]
+                                            ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_double, _F64P, _I32P, _I32P, _F64P]
             lib.oracle_ccm_unit.restype = ctypes.c_int
             lib.oracle_ccm.argtypes = [_F32P, ctypes.c_int32, ctypes.c_int64, _I32P,
                                        ctypes.c_int32, _I32P, ctypes.c_int32, _I32P,
                                        ctypes.c_int32, _I64P, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_uint64, ctypes.c_int32, _F64P]
+                                       ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_double, _F64P]
             lib.oracle_ccm.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -116,22 +120,25 @@ def library(n_m: int, L: int, j: int, E: int, tau: int, k: int, seed: int) -> np
 
 
 def neighbours(s: np.ndarray, E: int, tau: int, lib: np.ndarray,
-               select_fp64: bool = False) -> np.ndarray:
-    """E+1 nearest library neighbours [N_m][E+1] of every manifold point of ``s``."""
+               select_fp64: bool = False, theiler: int = 0) -> np.ndarray:
+    """E+1 nearest library neighbours [N_m][E+1] of every manifold point of ``s``;
+    candidates of query m are the library points l with |l - m| > theiler."""
     s = _c(s, np.float32)
     lib = _c(lib, np.int32)
     n_m = len(s) - (E - 1) * tau
     out = np.zeros((n_m, E + 1), np.int32)
     rc = _load().oracle_neighbours(_ptr(s, _F32P), len(s), int(E), int(tau), _ptr(lib, _I32P),
-                                   len(lib), int(bool(select_fp64)), _ptr(out, _I32P))
+                                   len(lib), int(bool(select_fp64)), int(theiler),
+                                   _ptr(out, _I32P))
     if rc != 0:
         raise ValueError("invalid neighbour search arguments")
     return out
 
 
 def predict(lib_s: np.ndarray, tgt_s: np.ndarray, E: int, tau: int,
-            nbr: np.ndarray) -> np.ndarray:
-    """Simplex predictions Xhat [N_m] (FP64) from neighbour lists [N_m][E+1]."""
+            nbr: np.ndarray, weight_floor: float = 0.0) -> np.ndarray:
+    """Simplex predictions Xhat [N_m] (FP64) from neighbour lists [N_m][E+1];
+    u_i = max(exp(-d_i/d_1), weight_floor)."""
     lib_s = _c(lib_s, np.float32)
     tgt_s = _c(tgt_s, np.float32)
     nbr = _c(nbr, np.int32)
@@ -139,14 +146,16 @@ def predict(lib_s: np.ndarray, tgt_s: np.ndarray, E: int, tau: int,
     assert nbr.shape == (n_m, E + 1)
     out = np.zeros(n_m, np.float64)
     rc = _load().oracle_predict(_ptr(lib_s, _F32P), _ptr(tgt_s, _F32P), len(lib_s), int(E),
-                                int(tau), _ptr(nbr, _I32P), _ptr(out, _F64P))
+                                int(tau), float(weight_floor), _ptr(nbr, _I32P),
+                                _ptr(out, _F64P))
     if rc != 0:
         raise ValueError("invalid prediction arguments")
     return out
 
 
 def query_subset(lib_s: np.ndarray, tgt_s: np.ndarray, E: int, tau: int, lib: np.ndarray,
-                 queries, select_fp64: bool = False):
+                 queries, select_fp64: bool = False, theiler: int = 0,
+                 weight_floor: float = 0.0):
     """Neighbours [nq][E+1] and predictions [nq] of the listed query points only."""
     lib_s = _c(lib_s, np.float32)
     tgt_s = _c(tgt_s, np.float32)
@@ -156,7 +165,8 @@ def query_subset(lib_s: np.ndarray, tgt_s: np.ndarray, E: int, tau: int, lib: np
     xh = np.zeros(len(q), np.float64)
     rc = _load().oracle_query_subset(_ptr(lib_s, _F32P), _ptr(tgt_s, _F32P), len(lib_s), int(E),
                                      int(tau), _ptr(lib, _I32P), len(lib), _ptr(q, _I64P), len(q),
-                                     int(bool(select_fp64)), _ptr(nbr, _I32P), _ptr(xh, _F64P))
+                                     int(bool(select_fp64)), int(theiler), float(weight_floor),
+                                     _ptr(nbr, _I32P), _ptr(xh, _F64P))
     if rc != 0:
         raise ValueError("invalid query subset arguments")
     return nbr, xh
@@ -177,7 +187,8 @@ def skill(tgt_s: np.ndarray, E: int, tau: int, xhat: np.ndarray) -> float:
 
 
 def ccm_unit(series: np.ndarray, j: int, i: int, E: int, tau: int, L: int, k: int, seed: int,
-             select_fp64: bool = False, keep: bool = False):
+             select_fp64: bool = False, keep: bool = False, theiler: int = 0,
+             weight_floor: float = 0.0):
     """rho of one unit; with ``keep`` also (library, neighbours, Xhat)."""
     series = _c(series, np.float32)
     V, n = series.shape
@@ -188,7 +199,7 @@ def ccm_unit(series: np.ndarray, j: int, i: int, E: int, tau: int, L: int, k: in
     xh = np.zeros(max(n_m, 0), np.float64) if keep else None
     rc = _load().oracle_ccm_unit(
         _ptr(series, _F32P), V, n, int(j), int(i), int(E), int(tau), int(L), int(k), int(seed),
-        int(bool(select_fp64)), _ptr(rho, _F64P),
+        int(bool(select_fp64)), int(theiler), float(weight_floor), _ptr(rho, _F64P),
         _ptr(lib, _I32P) if keep else None, _ptr(nbr, _I32P) if keep else None,
         _ptr(xh, _F64P) if keep else None)
     if rc != 0:
@@ -198,7 +209,8 @@ def ccm_unit(series: np.ndarray, j: int, i: int, E: int, tau: int, L: int, k: in
     return float(rho[0])
 
 
-def ccm(series, pairs, E, tau, L, r: int, seed: int, select_fp64: bool = False) -> np.ndarray:
+def ccm(series, pairs, E, tau, L, r: int, seed: int, select_fp64: bool = False,
+        theiler: int = 0, weight_floor: float = 0.0) -> np.ndarray:
     """Whole sweep: rho [n_pairs][n_E][n_tau][n_L][r] (FP64)."""
     series = _c(series, np.float32)
     pairs = _c(pairs, np.int32).reshape(-1, 2)
@@ -209,7 +221,8 @@ def ccm(series, pairs, E, tau, L, r: int, seed: int, select_fp64: bool = False) 
     out = np.zeros((len(pairs), len(E), len(tau), len(L), int(r)), np.float64)
     rc = _load().oracle_ccm(_ptr(series, _F32P), V, n, _ptr(pairs, _I32P), len(pairs),
                             _ptr(E, _I32P), len(E), _ptr(tau, _I32P), len(tau), _ptr(L, _I64P),
-                            len(L), int(r), int(seed), int(bool(select_fp64)), _ptr(out, _F64P))
+                            len(L), int(r), int(seed), int(bool(select_fp64)), int(theiler),
+                            float(weight_floor), _ptr(out, _F64P))
     if rc != 0:
         raise ValueError("invalid CCM problem")
     return out

@@ -17,6 +17,14 @@
 //   * simplex projection (Sect. 2.1): u_i = exp(-d_i/d_1), w_i = u_i / sum u,
 //     Xhat(t) = sum w_i X(t_i);
 //   * skill = Pearson correlation of X and Xhat (Sect. 2.1).
+// Two options that the paper does not discuss but common CCM implementations
+// carry, both off by default (the paper's method):
+//   * an exclusion (Theiler) window W >= 0: a library point l is a neighbour
+//     candidate of query m only when |l - m| > W (W = 0: only m itself is
+//     excluded, the paper's rule), so that points close in time do not
+//     predict each other;
+//   * a weight floor f >= 0: u_i = max(exp(-d_i/d_1), f) before the
+//     normalisation, so that a far neighbour keeps a small positive weight.
 //
 // Precision: the neighbour selection can be taken on FP32 squared distances
 // accumulated in coordinate order with one rounding per fused multiply-add
@@ -139,13 +147,13 @@ double sqdist_fp64(const float* s, int32_t E, int32_t tau, int64_t a, int64_t b)
 // distance 0 stays eligible.
 // ---------------------------------------------------------------------------
 void query_neighbours(const float* s, int32_t E, int32_t tau, const int32_t* lib, int64_t L,
-                      int32_t select_fp64, int64_t m, std::vector<std::pair<double, int32_t>>* cand,
-                      int32_t* nbr_row) {
+                      int32_t select_fp64, int32_t theiler, int64_t m,
+                      std::vector<std::pair<double, int32_t>>* cand, int32_t* nbr_row) {
   const int32_t kk = E + 1;
   cand->clear();
   for (int64_t q = 0; q < L; ++q) {
     const int32_t l = lib[q];
-    if (l == m) continue;
+    if (std::llabs((long long)l - (long long)m) <= theiler) continue;  // m itself when W = 0
     const double d2 = select_fp64 ? sqdist_fp64(s, E, tau, m, l)
                                   : (double)sqdist_fp32(s, E, tau, m, l);
     cand->push_back(std::make_pair(d2, l));
@@ -155,22 +163,22 @@ void query_neighbours(const float* s, int32_t E, int32_t tau, const int32_t* lib
 }
 
 void neighbours(const float* s, int64_t n, int32_t E, int32_t tau, const int32_t* lib,
-                int64_t L, int32_t select_fp64, int32_t* nbr) {
+                int64_t L, int32_t select_fp64, int32_t theiler, int32_t* nbr) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
   std::vector<std::pair<double, int32_t>> cand;
   cand.reserve((size_t)L);
   for (int64_t m = 0; m < n_m; ++m)
-    query_neighbours(s, E, tau, lib, L, select_fp64, m, &cand, nbr + m * (E + 1));
+    query_neighbours(s, E, tau, lib, L, select_fp64, theiler, m, &cand, nbr + m * (E + 1));
 }
 
 // ---------------------------------------------------------------------------
 // Simplex projection (Sect. 2.1): FP64 distances d_1 <= ... <= d_{E+1} of the
 // given neighbours, u_i = exp(-d_i/d_1), w_i = u_i / sum u, Xhat = sum w_i
 // x[t_i].  When d_1 = 0, u_i is the limit of exp(-d_i/d_1) as d_1 -> 0+:
-// 1 for d_i = 0 and 0 otherwise.
+// 1 for d_i = 0 and 0 otherwise.  With a weight floor f, u_i = max(u_i, f).
 // ---------------------------------------------------------------------------
 double query_predict(const float* lib_s, const float* tgt_s, int32_t E, int32_t tau,
-                     const int32_t* nbr_row, int64_t m) {
+                     double weight_floor, const int32_t* nbr_row, int64_t m) {
   const int32_t kk = E + 1;
   std::vector<double> d((size_t)kk), u((size_t)kk);
   for (int32_t i = 0; i < kk; ++i) d[(size_t)i] = std::sqrt(sqdist_fp64(lib_s, E, tau, m, nbr_row[i]));
@@ -182,6 +190,7 @@ double query_predict(const float* lib_s, const float* tgt_s, int32_t E, int32_t 
       u[(size_t)i] = std::exp(-d[(size_t)i] / d1);
     else
       u[(size_t)i] = (d[(size_t)i] == 0.0) ? 1.0 : 0.0;
+    u[(size_t)i] = std::max(u[(size_t)i], weight_floor);
     usum += u[(size_t)i];
   }
   double acc = 0.0;
@@ -193,9 +202,17 @@ double query_predict(const float* lib_s, const float* tgt_s, int32_t E, int32_t 
 }
 
 void predict(const float* lib_s, const float* tgt_s, int64_t n, int32_t E, int32_t tau,
-             const int32_t* nbr, double* xhat) {
+             double weight_floor, const int32_t* nbr, double* xhat) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
-  for (int64_t m = 0; m < n_m; ++m) xhat[m] = query_predict(lib_s, tgt_s, E, tau, nbr + m * (E + 1), m);
+  for (int64_t m = 0; m < n_m; ++m)
+    xhat[m] = query_predict(lib_s, tgt_s, E, tau, weight_floor, nbr + m * (E + 1), m);
+}
+
+// Option check shared by the entry points: W >= 0 with every query keeping at
+// least E+1 candidates (L >= E + 2 + 2W), and a finite floor f >= 0.
+bool options_ok(int32_t E, int64_t L, int32_t theiler, double weight_floor) {
+  return theiler >= 0 && L >= (int64_t)E + 2 + 2 * (int64_t)theiler &&
+         std::isfinite(weight_floor) && weight_floor >= 0.0;
 }
 
 // Pearson correlation, two passes in FP64; NaN when either variance is 0.
@@ -239,20 +256,22 @@ int oracle_library(int64_t n_m, int64_t L, int32_t j, int32_t E, int32_t tau, in
 
 // E+1 nearest neighbours [N_m][E+1] of every manifold point of series s.
 int oracle_neighbours(const float* s, int64_t n, int32_t E, int32_t tau, const int32_t* lib,
-                      int64_t L, int32_t select_fp64, int32_t* nbr_out) {
+                      int64_t L, int32_t select_fp64, int32_t theiler, int32_t* nbr_out) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
   if (E < 1 || tau < 1 || n_m < 1 || L < E + 2 || L > n_m) return -1;
-  neighbours(s, n, E, tau, lib, L, select_fp64, nbr_out);
+  if (!options_ok(E, L, theiler, 0.0)) return -1;
+  neighbours(s, n, E, tau, lib, L, select_fp64, theiler, nbr_out);
   return 0;
 }
 
 // Simplex predictions [N_m] from given neighbour lists (also the "replay" of
 // a neighbour set found elsewhere).
 int oracle_predict(const float* lib_s, const float* tgt_s, int64_t n, int32_t E, int32_t tau,
-                   const int32_t* nbr, double* xhat_out) {
+                   double weight_floor, const int32_t* nbr, double* xhat_out) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
   if (E < 1 || tau < 1 || n_m < 1) return -1;
-  predict(lib_s, tgt_s, n, E, tau, nbr, xhat_out);
+  if (!std::isfinite(weight_floor) || weight_floor < 0.0) return -1;
+  predict(lib_s, tgt_s, n, E, tau, weight_floor, nbr, xhat_out);
   return 0;
 }
 
@@ -260,15 +279,19 @@ int oracle_predict(const float* lib_s, const float* tgt_s, int64_t n, int32_t E,
 // (for checking sampled outputs of large problems).
 int oracle_query_subset(const float* lib_s, const float* tgt_s, int64_t n, int32_t E, int32_t tau,
                         const int32_t* lib, int64_t L, const int64_t* queries, int64_t nq,
-                        int32_t select_fp64, int32_t* nbr_out, double* xhat_out) {
+                        int32_t select_fp64, int32_t theiler, double weight_floor,
+                        int32_t* nbr_out, double* xhat_out) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
   if (E < 1 || tau < 1 || n_m < 1 || L < E + 2 || L > n_m) return -1;
+  if (!options_ok(E, L, theiler, weight_floor)) return -1;
   std::vector<std::pair<double, int32_t>> cand;
   cand.reserve((size_t)L);
   for (int64_t q = 0; q < nq; ++q) {
     if (queries[q] < 0 || queries[q] >= n_m) return -1;
-    query_neighbours(lib_s, E, tau, lib, L, select_fp64, queries[q], &cand, nbr_out + q * (E + 1));
-    xhat_out[q] = query_predict(lib_s, tgt_s, E, tau, nbr_out + q * (E + 1), queries[q]);
+    query_neighbours(lib_s, E, tau, lib, L, select_fp64, theiler, queries[q], &cand,
+                     nbr_out + q * (E + 1));
+    xhat_out[q] = query_predict(lib_s, tgt_s, E, tau, weight_floor, nbr_out + q * (E + 1),
+                                queries[q]);
   }
   return 0;
 }
@@ -287,17 +310,19 @@ double oracle_skill(const float* tgt_s, int64_t n, int32_t E, int32_t tau, const
 // library [L], neighbours [N_m][E+1], predictions [N_m] (pass NULL to skip).
 int oracle_ccm_unit(const float* series, int32_t V, int64_t n, int32_t j, int32_t i, int32_t E,
                     int32_t tau, int64_t L, int32_t k, uint64_t seed, int32_t select_fp64,
-                    double* rho_out, int32_t* lib_out, int32_t* nbr_out, double* xhat_out) {
+                    int32_t theiler, double weight_floor, double* rho_out, int32_t* lib_out,
+                    int32_t* nbr_out, double* xhat_out) {
   const int64_t n_m = n - (int64_t)(E - 1) * tau;
   if (j < 0 || j >= V || i < 0 || i >= V || i == j) return -1;
   if (E < 1 || E > 10 || tau < 1 || n_m < 1 || L < E + 2 || L > n_m || k < 0) return -1;
+  if (!options_ok(E, L, theiler, weight_floor)) return -1;
   const float* s_j = series + (int64_t)j * n;
   const float* s_i = series + (int64_t)i * n;
   std::vector<int32_t> lib((size_t)L), nbr((size_t)(n_m * (E + 1)));
   std::vector<double> xhat((size_t)n_m);
   sample_library(n_m, L, j, E, tau, k, seed, lib.data());
-  neighbours(s_j, n, E, tau, lib.data(), L, select_fp64, nbr.data());
-  predict(s_j, s_i, n, E, tau, nbr.data(), xhat.data());
+  neighbours(s_j, n, E, tau, lib.data(), L, select_fp64, theiler, nbr.data());
+  predict(s_j, s_i, n, E, tau, weight_floor, nbr.data(), xhat.data());
   std::vector<double> x((size_t)n_m);
   observed(s_i, n, E, tau, x.data());
   *rho_out = pearson(x.data(), xhat.data(), n_m);
@@ -311,7 +336,7 @@ int oracle_ccm_unit(const float* series, int32_t V, int64_t n, int32_t j, int32_
 int oracle_ccm(const float* series, int32_t V, int64_t n, const int32_t* pairs, int32_t n_pairs,
                const int32_t* Es, int32_t n_E, const int32_t* taus, int32_t n_tau,
                const int64_t* Ls, int32_t n_L, int32_t r, uint64_t seed, int32_t select_fp64,
-               double* rho_out) {
+               int32_t theiler, double weight_floor, double* rho_out) {
   int64_t o = 0;
   for (int32_t p = 0; p < n_pairs; ++p)
     for (int32_t e = 0; e < n_E; ++e)
@@ -319,8 +344,8 @@ int oracle_ccm(const float* series, int32_t V, int64_t n, const int32_t* pairs, 
         for (int32_t l = 0; l < n_L; ++l)
           for (int32_t k = 0; k < r; ++k) {
             const int rc = oracle_ccm_unit(series, V, n, pairs[2 * p], pairs[2 * p + 1], Es[e],
-                                           taus[t], Ls[l], k, seed, select_fp64, &rho_out[o],
-                                           nullptr, nullptr, nullptr);
+                                           taus[t], Ls[l], k, seed, select_fp64, theiler,
+                                           weight_floor, &rho_out[o], nullptr, nullptr, nullptr);
             if (rc != 0) return rc;
             ++o;
           }
