@@ -15,10 +15,12 @@
  *       ((hi32(Philox4x64-10(ctr=(m, k, L, (j<<16)|(E<<8)|tau),
  *       key=(seed, 0)).word0)) << 32 | m) is among the L smallest;
  *     - for every manifold point m (all N_m points are queries) its E+1
- *       nearest library points, m itself excluded, ordered by (squared FP32
+ *       nearest library points, m itself excluded (optionally every l with
+ *       |l - m| <= W, ccm_problem.theiler), ordered by (squared FP32
  *       distance, manifold index) (Sect. 3.2);
  *     - simplex projection (Sect. 2.1): d_i the distances, u_i =
  *       exp(-d_i/d_1) (the limit 1 for d_i = 0, else 0, when d_1 = 0),
+ *       optionally raised to a floor f (ccm_problem.weight_floor),
  *       w_i = u_i / sum u, Xhat(m) = sum_i w_i s_i[t_i];
  *     - the skill rho = Pearson(s_i[t_m], Xhat(m)) over m (Sect. 2.1),
  *       accumulated in FP64; NaN when either variance is zero.
@@ -80,7 +82,15 @@ typedef struct {
   const int64_t* L;        /* [n_L], each E+2 <= L <= N_m for every (E, tau) of the grid */
   int32_t r;               /* realizations per (pair, E, tau, L) cell, >= 1 */
   uint64_t seed;           /* library sampler seed */
-  uint32_t flags;          /* CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE */
+  uint32_t flags;          /* CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE | ... */
+  /* Two options the paper does not discuss (common CCM variants); zero for the
+   * paper's method.  theiler: exclusion window W >= 0, library point l is a
+   * neighbour candidate of query m only when |l - m| > W (W = 0 excludes m
+   * itself, the paper's rule); needs L >= E + 2 + 2W for every cell.
+   * weight_floor: f >= 0, finite; u_i = max(exp(-d_i/d_1), f) before the
+   * weights are normalised (f is applied in FP32). */
+  int32_t theiler;
+  float weight_floor;
 } ccm_problem;
 
 /* Optional per-unit outputs for checking (all device or all host, following

@@ -53,7 +53,8 @@ class ccm_problem(ctypes.Structure):
                 ("n_E", ctypes.c_int32), ("E", ctypes.POINTER(ctypes.c_int32)),
                 ("n_tau", ctypes.c_int32), ("tau", ctypes.POINTER(ctypes.c_int32)),
                 ("n_L", ctypes.c_int32), ("L", ctypes.POINTER(ctypes.c_int64)),
-                ("r", ctypes.c_int32), ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+                ("r", ctypes.c_int32), ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("theiler", ctypes.c_int32), ("weight_floor", ctypes.c_float)]
 
 
 class ccm_debug_out(ctypes.Structure):
@@ -155,7 +156,7 @@ def _stream(s) -> Optional[int]:
     return int(s)
 
 
-def _problem(series_shape, pairs, E, tau, L, r, seed, flags, keep):
+def _problem(series_shape, pairs, E, tau, L, r, seed, flags, keep, theiler=0, weight_floor=0.0):
     pairs = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 2))
     E = np.ascontiguousarray(np.asarray(E, np.int32).reshape(-1))
     tau = np.ascontiguousarray(np.asarray(tau, np.int32).reshape(-1))
@@ -167,7 +168,7 @@ def _problem(series_shape, pairs, E, tau, L, r, seed, flags, keep):
                        len(E), E.ctypes.data_as(P(ctypes.c_int32)),
                        len(tau), tau.ctypes.data_as(P(ctypes.c_int32)),
                        len(L), L.ctypes.data_as(P(ctypes.c_int64)), int(r), int(seed),
-                       int(flags))
+                       int(flags), int(theiler), float(weight_floor))
 
 
 def ccm_context_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
@@ -180,9 +181,10 @@ def ccm_context_destroy(ctx: int) -> None:
     _check(_lib.ccm_context_destroy(ctx))
 
 
-def ccm_plan(ctx: int, series_shape, pairs, E, tau, L, r: int, seed: int, flags: int = 0) -> int:
+def ccm_plan(ctx: int, series_shape, pairs, E, tau, L, r: int, seed: int, flags: int = 0,
+             theiler: int = 0, weight_floor: float = 0.0) -> int:
     keep: list = []
-    prob = _problem(series_shape, pairs, E, tau, L, r, seed, flags, keep)
+    prob = _problem(series_shape, pairs, E, tau, L, r, seed, flags, keep, theiler, weight_floor)
     h = ctypes.c_void_p()
     _check(_lib.ccm_plan(ctx, ctypes.byref(prob), ctypes.byref(h)))
     return h.value
@@ -227,10 +229,11 @@ def ccm_run_plain(plan: int, series, rho, stream=None) -> None:
     _check(_lib.ccm_run_plain(plan, _ptr(series), _ptr(rho), _stream(stream)))
 
 
-def ccm_submit(ctx: int, series, pairs, E, tau, L, r: int, seed: int) -> int:
+def ccm_submit(ctx: int, series, pairs, E, tau, L, r: int, seed: int, theiler: int = 0,
+               weight_floor: float = 0.0) -> int:
     keep: list = []
     series = np.ascontiguousarray(series, dtype=np.float32)
-    prob = _problem(series.shape, pairs, E, tau, L, r, seed, 0, keep)
+    prob = _problem(series.shape, pairs, E, tau, L, r, seed, 0, keep, theiler, weight_floor)
     t = ctypes.c_uint64()
     _check(_lib.ccm_submit(ctx, ctypes.byref(prob), _ptr(series), ctypes.byref(t)))
     return t.value
@@ -262,9 +265,11 @@ def ccm_run_noalloc(d_series, j: int, i: int, E: int, tau: int, L: int, r: int, 
 
 
 def plan_problem(ctx: int, problem, flags: int = 0) -> int:
-    """ccm_plan for an object with series, pairs, E, tau, L, r and seed attributes."""
+    """ccm_plan for an object with series, pairs, E, tau, L, r and seed attributes
+    (and optionally theiler and weight_floor)."""
     return ccm_plan(ctx, problem.series.shape, problem.pairs, problem.E, problem.tau, problem.L,
-                    problem.r, problem.seed, flags)
+                    problem.r, problem.seed, flags, getattr(problem, "theiler", 0),
+                    getattr(problem, "weight_floor", 0.0))
 
 
 def rho_shape(problem) -> tuple:

@@ -29,6 +29,8 @@ struct UnitDesc {
   int32_t n_tiles;      // query tiles of the fused kernel
   int32_t n_targets;    // targets cross-mapped from this library (>= 1)
   int32_t table_R;      // > 0: neighbours read from the table (R entries per query)
+  int32_t theiler;      // exclusion window W >= 0: candidates l of query m need |l - m| > W
+  float wfloor;         // simplex weight floor f >= 0: u_i = max(u_i, f)
   int32_t pad;
 };
 
@@ -68,6 +70,7 @@ struct TableJob {
   int32_t pad;
 };
 constexpr int kTableMaxR = 2048;       // entries per query row, at most
+constexpr int kTableChunk = 8;         // query tiles per table work item (one bitmap each)
 
 // Sampler: one CTA per unit.
 struct SamplerParams {

@@ -11,25 +11,27 @@
 // Design (GB300, FP32 on the CUDA cores; E <= 10 is not a dense contraction):
 //  * persistent CTAs pull (realization, query tile) items, sorted by cost,
 //    from an atomic counter;
-//  * each thread owns two queries whose coordinates sit packed in f32x2
-//    registers, so one sub.f32x2 + fma.f32x2 pair advances both queries;
-//  * the library is staged through shared memory tile by tile, each
-//    coordinate stored twice ({c, c}) so that a broadcast 128-bit load feeds
-//    the packed operations directly;
+//  * each thread owns one query; library points sit in shared memory in
+//    pairs, packed {a_e, b_e} per coordinate, so one sub.f32x2 + fma.f32x2
+//    pair advances the query's distances to two points;
+//  * the library is staged through shared memory tile by tile; a broadcast
+//    128-bit load feeds the packed operations directly;
 //  * squared distances are accumulated in coordinate order (first term a
 //    rounded product, then one fused multiply-add per coordinate), the same
 //    rounding sequence the FP32 selection is defined by;
-//  * each query keeps its E+2 best (squared distance, index) in registers,
-//    sorted; candidates under the current threshold are appended to a small
-//    per-query buffer in shared memory and merged, warp-wide, when a buffer
-//    runs full, so a rare insertion in one lane does not stall the warp for a
-//    full sorted insertion every time;
+//  * each query keeps its E+1 best (squared distance, index) in registers,
+//    sorted; candidates under the current threshold (and outside the
+//    exclusion window, which always holds the query itself) are appended to
+//    a small per-query buffer in shared memory and merged, warp-wide, when a
+//    buffer runs full, so a rare insertion in one lane does not stall the
+//    warp for a full sorted insertion every time;
 //  * the library is visited in ascending manifold index, so a strict "<"
 //    during insertion keeps equal distances in index order;
-//  * the epilogue drops the query itself, forms u_i = exp(-d_i/d_1), the
-//    prediction, and FP64 moments; the last tile of a realization to finish
-//    merges the tiles' moments in tile order (Chan et al. pairwise update),
-//    so rho does not depend on the schedule.
+//  * the epilogue forms u_i = exp(-d_i/d_1) (optionally floored), the
+//    prediction, and the tile's FP64 moments (one warp does the FP64 work:
+//    the FP64 pipe is the scarce unit); the last tile of a realization to
+//    finish merges the tiles' moments in a fixed order, so rho does not
+//    depend on the schedule.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -153,52 +155,109 @@ __device__ __forceinline__ void insert_sorted(float (&kd)[K], int (&kl)[K], floa
   kl[0] = below[0] ? lx : kl[0];
 }
 
-// Deterministic block sum of three doubles; every thread gets the totals.
-// Explicit round-to-nearest adds: the same bits in every kernel that inlines it.
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* s_red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Butterfly sum over the warp: every lane ends with the same bits (each
+// level adds the same two values in either order).
+__device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a = __dadd_rn(a, __shfl_xor_sync(kFull, a, o));
-    b = __dadd_rn(b, __shfl_xor_sync(kFull, b, o));
-    c = __dadd_rn(c, __shfl_xor_sync(kFull, c, o));
-  }
-  if (lane == 0) {
-    s_red[3 * warp + 0] = a;
-    s_red[3 * warp + 1] = b;
-    s_red[3 * warp + 2] = c;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double ta = 0.0, tb = 0.0, tc = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      ta = __dadd_rn(ta, s_red[3 * w + 0]);
-      tb = __dadd_rn(tb, s_red[3 * w + 1]);
-      tc = __dadd_rn(tc, s_red[3 * w + 2]);
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// Two-pass FP64 moments of one tile's (observed, predicted) pairs, staged in
+// shared memory (xs[0..nq), ys[0..nq)), by one warp: each lane sums a fixed
+// strided subset, then the butterfly.  Writes (n, mean_x, mean_y, Sxx, Syy,
+// Sxy) about the tile means.  One warp does the FP64 work that would
+// otherwise occupy all eight: the FP64 pipe is the scarce unit here.
+__device__ __forceinline__ void tile_moments(const double* xs, const double* ys, int nq,
+                                             double* part) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kPer = kQT / 32;
+  double sx = 0.0, sy = 0.0;
+#pragma unroll
+  for (int c = 0; c < kPer; ++c) {
+    const int i = lane + 32 * c;
+    if (i < nq) {
+      sx = __dadd_rn(sx, xs[i]);
+      sy = __dadd_rn(sy, ys[i]);
     }
-    s_red[3 * (kThreads / 32) + 0] = ta;
-    s_red[3 * (kThreads / 32) + 1] = tb;
-    s_red[3 * (kThreads / 32) + 2] = tc;
   }
-  __syncthreads();
-  a = s_red[3 * (kThreads / 32) + 0];
-  b = s_red[3 * (kThreads / 32) + 1];
-  c = s_red[3 * (kThreads / 32) + 2];
-  __syncthreads();
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  const double n = (double)nq;
+  const double mx = __ddiv_rn(sx, n), my = __ddiv_rn(sy, n);
+  double sxx = 0.0, syy = 0.0, sxy = 0.0;
+#pragma unroll
+  for (int c = 0; c < kPer; ++c) {
+    const int i = lane + 32 * c;
+    if (i < nq) {  // second pass re-reads shared memory: registers are scarce here
+      const double a = __dsub_rn(xs[i], mx), b = __dsub_rn(ys[i], my);
+      sxx = __fma_rn(a, a, sxx);
+      syy = __fma_rn(b, b, syy);
+      sxy = __fma_rn(a, b, sxy);
+    }
+  }
+  sxx = warp_sum(sxx);
+  syy = warp_sum(syy);
+  sxy = warp_sum(sxy);
+  if (lane == 0) {
+    part[0] = n;
+    part[1] = mx;
+    part[2] = my;
+    part[3] = sxx;
+    part[4] = syy;
+    part[5] = sxy;
+  }
+}
+
+// Merge the tile moments of one (realization, target) into rho, by one warp.
+// With the grand means MX = sum(n_t mx_t)/N, the centred sums are exactly
+//   Sxx = sum_t [Sxx_t + n_t (mx_t - MX)^2]   (likewise Syy, Sxy),
+// a sum of non-negative terms (no cancellation), taken in a fixed lane and
+// butterfly order: rho does not depend on which CTA ran which tile, or when.
+__device__ __forceinline__ double merge_moments(const double* base, int n_tiles) {
+  const int lane = threadIdx.x & 31;
+  double N = 0.0, SX = 0.0, SY = 0.0;
+  for (int q = lane; q < n_tiles; q += 32) {
+    const double* pt = base + 6 * q;
+    const double nq = __ldcg(pt + 0);
+    N = __dadd_rn(N, nq);
+    SX = __fma_rn(nq, __ldcg(pt + 1), SX);
+    SY = __fma_rn(nq, __ldcg(pt + 2), SY);
+  }
+  N = warp_sum(N);
+  SX = warp_sum(SX);
+  SY = warp_sum(SY);
+  const double MX = __ddiv_rn(SX, N), MY = __ddiv_rn(SY, N);
+  double SXX = 0.0, SYY = 0.0, SXY = 0.0;
+  for (int q = lane; q < n_tiles; q += 32) {
+    const double* pt = base + 6 * q;
+    const double nq = __ldcg(pt + 0);
+    const double dx = __dsub_rn(__ldcg(pt + 1), MX), dy = __dsub_rn(__ldcg(pt + 2), MY);
+    const double wx = __dmul_rn(nq, dx);
+    SXX = __fma_rn(wx, dx, __dadd_rn(SXX, __ldcg(pt + 3)));
+    SYY = __fma_rn(__dmul_rn(nq, dy), dy, __dadd_rn(SYY, __ldcg(pt + 4)));
+    SXY = __fma_rn(wx, dy, __dadd_rn(SXY, __ldcg(pt + 5)));
+  }
+  SXX = warp_sum(SXX);
+  SYY = warp_sum(SYY);
+  SXY = warp_sum(SXY);
+  return (SXX > 0.0 && SYY > 0.0) ? __ddiv_rn(SXY, __dsqrt_rn(__dmul_rn(SXX, SYY))) : nan("");
 }
 
 // Everything after the neighbour search, shared by the brute-force and the
 // table paths: dd[0..E] ascending FP32 squared distances and nb[0..E] the
 // neighbours of query m (itself excluded).  Simplex weights, the prediction
-// of every target, FP64 tile moments, and the in-order merge of the moments
-// by the realization's last tile.
+// of every target, FP64 tile moments, and the merge of the moments by the
+// realization's last tile.  `stage` is 4*kQT doubles of shared memory that no
+// thread reads any more once every thread has arrived here.
 template <int E>
 __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& u, int unit,
                                             int tile, int m, bool valid, const float (&dd)[E + 1],
-                                            const int (&nb)[E + 1], double* s_red, int* s_last) {
-  const int tid = threadIdx.x;
+                                            const int (&nb)[E + 1], double* stage, int* s_last) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int n_m = u.n_m;
   const int off = (E - 1) * u.tau;
+  const int nq = min(kQT, n_m - tile * kQT);  // valid queries of this tile (>= 1)
   // Simplex weights (Sect. 2.1), once per query for every target.  Every
   // floating-point step below is an explicit round-to-nearest operation, so
   // the brute-force and table kernels (and every batch) produce the same bits.
@@ -209,11 +268,12 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
 #pragma unroll
   for (int s = 0; s <= E; ++s) {
     const float di = __fsqrt_rn(dd[s]);
-    w[s] = (d1 > 0.f) ? expf(-__fdiv_rn(di, d1)) : ((di == 0.f) ? 1.f : 0.f);
+    w[s] = fmaxf((d1 > 0.f) ? expf(-__fdiv_rn(di, d1)) : ((di == 0.f) ? 1.f : 0.f), u.wfloor);
     usum = __fadd_rn(usum, w[s]);
     // an unfilled slot (only possible with non-finite device input) reads in bounds
     nbc[s] = min(max(nb[s], 0), n_m - 1);
   }
+  __syncthreads();  // every thread is done with the search's shared memory
 
   for (int t = 0; t < u.n_targets; ++t) {
     const TargetDesc tg = p.targets[u.tgt_off + t];
@@ -222,8 +282,6 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
 #pragma unroll
     for (int s = 0; s <= E; ++s) acc = __fmaf_rn(w[s], si[nbc[s] + off], acc);
     const float xhat = __fdiv_rn(acc, usum);
-    const double xo = valid ? (double)si[m + off] : 0.0;
-    const double xp = valid ? (double)xhat : 0.0;
     if (valid) {
       if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
       if (p.dbg_nbr) {
@@ -231,32 +289,19 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
         for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nb[s];
       }
     }
-    // Tile moments of this target, two passes over the registers.
-    double n = valid ? 1.0 : 0.0, sx = xo, sy = xp;
-    block_sum3(n, sx, sy, s_red);
-    const double mx = __ddiv_rn(sx, n), my = __ddiv_rn(sy, n);
-    double sxx = 0.0, syy = 0.0, sxy = 0.0;
-    if (valid) {
-      const double a = __dsub_rn(xo, mx), b = __dsub_rn(xp, my);
-      sxx = __dmul_rn(a, a);
-      syy = __dmul_rn(b, b);
-      sxy = __dmul_rn(a, b);
-    }
-    block_sum3(sxx, syy, sxy, s_red);
-    if (tid == 0) {
-      double* part = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile);
-      part[0] = n;
-      part[1] = mx;
-      part[2] = my;
-      part[3] = sxx;
-      part[4] = syy;
-      part[5] = sxy;
-    }
+    // Double-buffered staging: warp 0 reduces target t while the others
+    // predict target t+1.  The barrier of target t+1 is reached by warp 0
+    // only after it has finished with target t-1's buffer.
+    double* buf = stage + (t & 1) * 2 * kQT;
+    buf[tid] = valid ? (double)si[m + off] : 0.0;
+    buf[kQT + tid] = valid ? (double)xhat : 0.0;
+    __syncthreads();
+    if (warp == 0)
+      tile_moments(buf, buf + kQT, nq, p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile));
   }
 
   // The last tile of this realization to finish merges every target's tile
-  // moments in tile order (Chan et al. pairwise update): rho does not depend
-  // on which CTA ran which tile, or when.
+  // moments (lane 0 of warp 0 wrote them all, before the fence).
   if (tid == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(&p.unit_done[unit], 1u);
@@ -265,25 +310,10 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   __syncthreads();
   if (*s_last) {
     __threadfence();
-    for (int t = tid; t < u.n_targets; t += kThreads) {
-      const double* base = p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles);
-      double N = __ldcg(base + 0), MX = __ldcg(base + 1), MY = __ldcg(base + 2);
-      double SXX = __ldcg(base + 3), SYY = __ldcg(base + 4), SXY = __ldcg(base + 5);
-      for (int q = 1; q < u.n_tiles; ++q) {
-        const double* pt = base + 6 * q;
-        const double nb2 = __ldcg(pt + 0), mxb = __ldcg(pt + 1), myb = __ldcg(pt + 2);
-        const double tot = __dadd_rn(N, nb2);
-        const double dx = __dsub_rn(mxb, MX), dy = __dsub_rn(myb, MY);
-        const double f = __ddiv_rn(__dmul_rn(N, nb2), tot);
-        SXX = __dadd_rn(SXX, __dadd_rn(__ldcg(pt + 3), __dmul_rn(__dmul_rn(dx, dx), f)));
-        SYY = __dadd_rn(SYY, __dadd_rn(__ldcg(pt + 4), __dmul_rn(__dmul_rn(dy, dy), f)));
-        SXY = __dadd_rn(SXY, __dadd_rn(__ldcg(pt + 5), __dmul_rn(__dmul_rn(dx, dy), f)));
-        MX = __dadd_rn(MX, __ddiv_rn(__dmul_rn(dx, nb2), tot));
-        MY = __dadd_rn(MY, __ddiv_rn(__dmul_rn(dy, nb2), tot));
-        N = tot;
-      }
-      p.rho[p.targets[u.tgt_off + t].out_idx] =
-          (SXX > 0.0 && SYY > 0.0) ? __ddiv_rn(SXY, __dsqrt_rn(__dmul_rn(SXX, SYY))) : nan("");
+    for (int t = warp; t < u.n_targets; t += kThreads / 32) {
+      const double r = merge_moments(p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles),
+                                     u.n_tiles);
+      if ((tid & 31) == 0) p.rho[p.targets[u.tgt_off + t].out_idx] = r;
     }
     if (tid == 0) p.unit_done[unit] = 0u;  // ready for the next run
   }
@@ -292,8 +322,8 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
 
 template <int E, int V>
 __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, int tile,
-                             unsigned char* smem, double* s_red, int* s_last) {
-  constexpr int K = E + 2;
+                             unsigned char* smem, int* s_last) {
+  constexpr int K = E + 1;  // the window keeps m itself out, so E+1 slots suffice
   constexpr int EP = TileShape<E>::EP;
   constexpr int LT = TileShape<E>::LT;
   u64* s_coord = reinterpret_cast<u64*>(smem);                                   // [LT/2][EP]
@@ -301,7 +331,7 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   int2* s_buf = reinterpret_cast<int2*>(smem + kCoordBytes);                     // [kBuf][kThreads]
 
   const int tid = threadIdx.x;
-  const int n_m = u.n_m, L = u.L, tau = u.tau;
+  const int n_m = u.n_m, L = u.L, tau = u.tau, W = u.theiler;
   const int off = (E - 1) * tau;
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
   const int32_t* lib = p.lib + u.lib_off;
@@ -389,8 +419,11 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
 #pragma unroll
       for (int pt = 0; pt < kStep; ++pt) {
         if (d[pt] < th) {
-          s_buf[cnt * kThreads + tid] = make_int2(__float_as_int(d[pt]), s_lidx[a + pt]);
-          ++cnt;
+          const int l = s_lidx[a + pt];
+          if (abs(l - m) > W) {  // exclusion window; W = 0 drops only m itself
+            s_buf[cnt * kThreads + tid] = make_int2(__float_as_int(d[pt]), l);
+            ++cnt;
+          }
         }
       }
       if (__any_sync(kFull, cnt >= merge_at)) merge_all();
@@ -398,18 +431,17 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   }
   merge_all();
 
-  // Epilogue: drop the query itself, simplex weights, prediction, moments.
-  int self = K;
-#pragma unroll
-  for (int s = 0; s < K; ++s) self = (kl[s] == m && self == K) ? s : self;
+  // Epilogue: the E+1 nearest (the window kept the query itself out of the
+  // list), simplex weights, prediction, moments.
   float dd[E + 1];
   int nb[E + 1];
 #pragma unroll
   for (int s = 0; s <= E; ++s) {
-    dd[s] = (s < self) ? kd[s] : kd[s + 1];
-    nb[s] = (s < self) ? kl[s] : kl[s + 1];
+    dd[s] = kd[s];
+    nb[s] = kl[s];
   }
-  finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, s_red, s_last);
+  // the library tile in shared memory is free once every thread is in the epilogue
+  finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, reinterpret_cast<double*>(smem), s_last);
 }
 
 // --------------------------------------------------------------------------
@@ -432,16 +464,24 @@ __device__ __forceinline__ float d2_point(const float* sj, int off, int tau, con
   return acc;
 }
 
+// Shared memory of the table kernel: the epilogue's staging buffer, the hits
+// of every query (slot-major, one column per thread), then the bitmap.
+constexpr int kStageBytes = 4 * kQT * 8;
+constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
+
 template <int E>
-__device__ void process_tile_table(const KnnParams& p, const UnitDesc& u, int unit, int tile,
-                                   unsigned char* smem, double* s_red, int* s_last) {
+__device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
+                                   unsigned char* smem, int* s_last) {
   const int tid = threadIdx.x;
-  const int n_m = u.n_m, L = u.L, tau = u.tau, R = u.table_R;
+  const int n_m = u.n_m, L = u.L, tau = u.tau, R = u.table_R, W = u.theiler;
   const int off = (E - 1) * tau;
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
   const int32_t* lib = p.lib + u.lib_off;
-  uint32_t* bm = reinterpret_cast<uint32_t*>(smem);  // library membership, one bit per point
+  double* stage = reinterpret_cast<double*>(smem);
+  int32_t* s_hit = reinterpret_cast<int32_t*>(smem + kStageBytes);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem + kStageBytes + kHitBytes);
   const int words = (n_m + 31) >> 5;
+  // Library membership, one bit per manifold point, once for the item's tiles.
   __syncthreads();  // the previous item's readers of bm are done
   for (int w = tid; w < words; w += kThreads) bm[w] = 0u;
   __syncthreads();
@@ -451,80 +491,84 @@ __device__ void process_tile_table(const KnnParams& p, const UnitDesc& u, int un
   }
   __syncthreads();
 
-  const int pos = tile * kQT + tid;
-  const bool valid = pos < n_m;
-  const int m = p.order[u.order_off + (valid ? pos : n_m - 1)];
-  float q[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
-
-  int nb[E + 1];
-#pragma unroll
-  for (int s2 = 0; s2 <= E; ++s2) nb[s2] = 0;
-  int found = valid ? 0 : E + 1;
-  const int64_t rowoff = u.table_off + (valid ? pos : 0);
-  const uint16_t* row16 = static_cast<const uint16_t*>(p.table) + rowoff;
-  const int32_t* row32 = static_cast<const int32_t*>(p.table) + rowoff;
+  const int tile1 = min(u.n_tiles, tile0 + kTableChunk);
+  const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u.table_off;
+  const int32_t* t32 = static_cast<const int32_t*>(p.table) + u.table_off;
   constexpr int kFlight = 8;  // table loads in flight per lane
-  int r = 0;
-  while (__any_sync(kFull, found <= E && r < R)) {
-    int idx[kFlight];
+  for (int tile = tile0; tile < tile1; ++tile) {
+    const int pos = tile * kQT + tid;
+    const bool valid = pos < n_m;
+    const int m = p.order[u.order_off + (valid ? pos : n_m - 1)];
+    float q[E];
 #pragma unroll
-    for (int c = 0; c < kFlight; ++c) {
-      const bool want = found <= E && r + c < R;
-      const int64_t o = (int64_t)(r + c) * n_m;
-      idx[c] = !want ? -1 : (p.table_u16 ? (int)__ldg(row16 + o) : __ldg(row32 + o));
-    }
+    for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
+
+    // Walk the row: the first E+1 members (other than m) are the neighbours,
+    // in (distance, index) order.  A hit goes to this thread's column of s_hit.
+    int found = valid ? 0 : E + 1;
+    const int col = valid ? pos : 0;
+    int r = 0;
+    while (__any_sync(kFull, found <= E && r < R)) {
+      int idx[kFlight];
 #pragma unroll
-    for (int c = 0; c < kFlight; ++c) {
-      const int x = idx[c];
-      if (found <= E && x >= 0 && x != m && ((bm[x >> 5] >> (x & 31)) & 1u)) {
-#pragma unroll
-        for (int s2 = 0; s2 <= E; ++s2) nb[s2] = (found == s2) ? x : nb[s2];
-        ++found;
+      for (int c = 0; c < kFlight; ++c) {
+        const bool want = found <= E && r + c < R;
+        const int64_t o = (int64_t)(r + c) * n_m + col;
+        idx[c] = !want ? -1 : (p.table_u16 ? (int)__ldg(t16 + o) : __ldg(t32 + o));
       }
-    }
-    r += kFlight;
-  }
-  if (found <= E) {
-    // Rare: fewer than E+1 members among the R nearest points; scan the
-    // library (ascending index, strict insertion keeps (d2, index) order).
-    float kd[E + 1];
-    int kl[E + 1];
 #pragma unroll
-    for (int s2 = 0; s2 <= E; ++s2) {
-      kd[s2] = INFINITY;
-      kl[s2] = -1;
-    }
-    // A plain shifting insertion (the branch-free insert_sorted variant
-    // produced wrong threshold updates in this kernel's rare path).
-    for (int a = 0; a < L; ++a) {
-      const int l = lib[a];
-      if (l == m) continue;
-      const float d = d2_point<E>(sj, off, tau, q, l);
-      if (d < kd[E]) {
-        int s2 = E;
-        while (s2 > 0 && d < kd[s2 - 1]) {
-          kd[s2] = kd[s2 - 1];
-          kl[s2] = kl[s2 - 1];
-          --s2;
+      for (int c = 0; c < kFlight; ++c) {
+        const int x = idx[c];
+        if (found <= E && x >= 0 && abs(x - m) > W && ((bm[x >> 5] >> (x & 31)) & 1u)) {
+          s_hit[found * kThreads + tid] = x;
+          ++found;
         }
-        kd[s2] = d;
-        kl[s2] = l;
       }
+      r += kFlight;
     }
+    int nb[E + 1];
+    if (found > E) {
 #pragma unroll
-    for (int s2 = 0; s2 <= E; ++s2) nb[s2] = kl[s2];
+      for (int s2 = 0; s2 <= E; ++s2) nb[s2] = valid ? s_hit[s2 * kThreads + tid] : 0;
+    } else {
+      // Rare: fewer than E+1 members among the R nearest points; scan the
+      // library (ascending index; the strict "<" keeps equal distances in
+      // index order).
+      float kd[E + 1];
+      int kl[E + 1];
+#pragma unroll
+      for (int s2 = 0; s2 <= E; ++s2) {
+        kd[s2] = INFINITY;
+        kl[s2] = -1;
+      }
+      for (int a = 0; a < L; ++a) {
+        const int l = lib[a];
+        if (abs(l - m) <= W) continue;
+        const float d = d2_point<E>(sj, off, tau, q, l);
+        if (d < kd[E]) {
+          int s2 = E;
+          while (s2 > 0 && d < kd[s2 - 1]) {
+            kd[s2] = kd[s2 - 1];
+            kl[s2] = kl[s2 - 1];
+            --s2;
+          }
+          kd[s2] = d;
+          kl[s2] = l;
+        }
+      }
+#pragma unroll
+      for (int s2 = 0; s2 <= E; ++s2) nb[s2] = kl[s2];
+    }
+    float dd[E + 1];
+#pragma unroll
+    for (int s2 = 0; s2 <= E; ++s2)
+      dd[s2] = valid ? d2_point<E>(sj, off, tau, q, max(nb[s2], 0)) : 0.f;
+    finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, stage, s_last);
   }
-  float dd[E + 1];
-#pragma unroll
-  for (int s2 = 0; s2 <= E; ++s2) dd[s2] = valid ? d2_point<E>(sj, off, tau, q, max(nb[s2], 0)) : 0.f;
-  finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, s_red, s_last);
 }
 
-__global__ void __launch_bounds__(kThreads) knn_table_kernel(KnnParams p) {
+__global__ void __launch_bounds__(kThreads, 3) knn_table_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double s_red[3 * (kThreads / 32) + 3];
   __shared__ int s_item, s_last;
   for (int64_t round = 0;; ++round) {
     if (p.persistent) {
@@ -538,7 +582,7 @@ __global__ void __launch_bounds__(kThreads) knn_table_kernel(KnnParams p) {
     const UnitDesc u = p.units[w.unit];
     switch (u.E) {
 #define CCM_TT(EV) \
-  case EV: process_tile_table<EV>(p, u, w.unit, w.tile, smem, s_red, &s_last); break;
+  case EV: process_table_item<EV>(p, u, w.unit, w.tile, smem, &s_last); break;
       CCM_TT(1) CCM_TT(2) CCM_TT(3) CCM_TT(4) CCM_TT(5)
       CCM_TT(6) CCM_TT(7) CCM_TT(8) CCM_TT(9) CCM_TT(10)
 #undef CCM_TT
@@ -550,19 +594,18 @@ __global__ void __launch_bounds__(kThreads) knn_table_kernel(KnnParams p) {
 
 template <int EMIN, int EMAX>
 __device__ __forceinline__ bool dispatch(int E, const KnnParams& p, const UnitDesc& u, int unit,
-                                         int tile, unsigned char* smem, double* s_red,
-                                         int* s_last) {
+                                         int tile, unsigned char* smem, int* s_last) {
   bool ok = false;
 #define CCM_CASE(EV)                                                    \
   if constexpr (EV >= EMIN && EV <= EMAX) {                             \
     if (E == EV) {                                                      \
       if constexpr (EV <= 6) {                                          \
         if (p.variant[EV] == 1)                                         \
-          process_tile<EV, 1>(p, u, unit, tile, smem, s_red, s_last);   \
+          process_tile<EV, 1>(p, u, unit, tile, smem, s_last);          \
         else                                                            \
-          process_tile<EV, 0>(p, u, unit, tile, smem, s_red, s_last);   \
+          process_tile<EV, 0>(p, u, unit, tile, smem, s_last);          \
       } else {                                                          \
-        process_tile<EV, 0>(p, u, unit, tile, smem, s_red, s_last);     \
+        process_tile<EV, 0>(p, u, unit, tile, smem, s_last);            \
       }                                                                 \
       ok = true;                                                        \
     }                                                                   \
@@ -576,7 +619,6 @@ __device__ __forceinline__ bool dispatch(int E, const KnnParams& p, const UnitDe
 template <int EMIN, int EMAX>
 __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double s_red[3 * (kThreads / 32) + 3];
   __shared__ int s_item, s_last;
   for (int64_t round = 0;; ++round) {
     if (p.persistent) {
@@ -588,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
     if ((int64_t)it >= p.n_items) break;
     const WorkItem w = p.items[it];
     const UnitDesc u = p.units[w.unit];
-    if (!dispatch<EMIN, EMAX>(u.E, p, u, w.unit, w.tile, smem, s_red, &s_last)) {
+    if (!dispatch<EMIN, EMAX>(u.E, p, u, w.unit, w.tile, smem, &s_last)) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
     }
   }
@@ -616,7 +658,9 @@ cudaError_t occupancy_range(int* ctas) {
 
 int knn_block_threads() { return kThreads; }
 
-size_t knn_table_smem(int max_nm) { return (size_t)((max_nm + 31) / 32) * 4 + 16; }
+size_t knn_table_smem(int max_nm) {
+  return (size_t)kStageBytes + kHitBytes + (size_t)((max_nm + 31) / 32) * 4 + 16;
+}
 
 cudaError_t knn_table_prepare(int max_nm) {
   return cudaFuncSetAttribute(knn_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -107,6 +107,8 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     u.n_targets = 1;
     u.table_off = 0;
     u.table_R = 0;
+    u.theiler = 0;
+    u.wfloor = 0.f;
     u.pad = 0;
     TargetDesc tg;
     tg.out_idx = k;

@@ -36,6 +36,7 @@ plain_knn_kernel(const float* series, const UnitDesc* unit, const TargetDesc* ta
   }
   for (int a = 0; a < u.L; ++a) {
     const int l = ul[a];
+    if (abs(l - m) <= u.theiler) continue;  // exclusion window (W = 0: m itself)
     float diff = __fsub_rn(q[0], sj[l + off]);
     float acc = __fmul_rn(diff, diff);
     for (int e = 1; e < E; ++e) {
@@ -53,22 +54,12 @@ plain_knn_kernel(const float* series, const UnitDesc* unit, const TargetDesc* ta
       kl[s] = l;
     }
   }
-  // drop the query itself, then simplex projection
-  int self = K;
-  for (int s = 0; s < K; ++s)
-    if (kl[s] == m) {
-      self = s;
-      break;
-    }
-  for (int s = self; s + 1 < K; ++s) {
-    kd[s] = kd[s + 1];
-    kl[s] = kl[s + 1];
-  }
+  // simplex projection over the E+1 nearest (the query was never a candidate)
   const float d1 = sqrtf(kd[0]);
   float usum = 0.f, accx = 0.f;
   for (int s = 0; s <= E; ++s) {
     const float di = sqrtf(kd[s]);
-    const float ui = (d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f);
+    const float ui = fmaxf((d1 > 0.f) ? expf(-di / d1) : ((di == 0.f) ? 1.f : 0.f), u.wfloor);
     usum += ui;
     const int nbc = min(max(kl[s], 0), u.n_m - 1);  // in bounds even for non-finite input
     accx = fmaf(ui, si[nbc + off], accx);

@@ -67,6 +67,8 @@ struct ProblemCopy {
   int32_t r = 0;
   uint64_t seed = 0;
   uint32_t flags = 0;
+  int32_t theiler = 0;
+  float weight_floor = 0.f;
 
   int64_t n_units() const {
     return (int64_t)(pairs.size() / 2) * (int64_t)E.size() * (int64_t)tau.size() *
@@ -91,6 +93,11 @@ ccm_status copy_problem(const ccm_problem* p, ProblemCopy* pc) {
   pc->r = p->r;
   pc->seed = p->seed;
   pc->flags = p->flags;
+  pc->theiler = p->theiler;
+  pc->weight_floor = p->weight_floor;
+  if (p->theiler < 0) return fail(CCM_EINVAL, "theiler window must be >= 0");
+  if (!std::isfinite(p->weight_floor) || p->weight_floor < 0.f)
+    return fail(CCM_EINVAL, "weight_floor must be finite and >= 0");
   for (int32_t q = 0; q < p->n_pairs; ++q) {
     const int32_t j = pc->pairs[2 * q], i = pc->pairs[2 * q + 1];
     if (j < 0 || j >= pc->V || i < 0 || i >= pc->V || i == j)
@@ -103,10 +110,14 @@ ccm_status copy_problem(const ccm_problem* p, ProblemCopy* pc) {
   for (int32_t E : pc->E)
     for (int32_t t : pc->tau) {
       const int64_t n_m = pc->n - (int64_t)(E - 1) * t;
-      for (int64_t L : pc->L)
+      for (int64_t L : pc->L) {
         if (L < E + 2 || L > n_m)
           return fail(CCM_EINVAL, "L=" + std::to_string(L) + " outside [E+2, N_m] for E=" +
                                       std::to_string(E) + ", tau=" + std::to_string(t));
+        if (L < (int64_t)E + 2 + 2 * (int64_t)pc->theiler)
+          return fail(CCM_EINVAL, "L=" + std::to_string(L) + " < E+2+2W for E=" +
+                                      std::to_string(E) + ", W=" + std::to_string(pc->theiler));
+      }
     }
   if ((double)pc->n_units() > 2.0e9) return fail(CCM_EINVAL, "too many realizations");
   return CCM_OK;
@@ -137,6 +148,16 @@ struct UnitList {
   int emin = kMaxE + 1, emax = 0, max_nm = 0;
   double pairs = 0.0, flops = 0.0;    // neighbour-search work actually done
 };
+
+// Smallest L whose realizations read a distance indexing table.  A table
+// scan visits about (E+1)*N_m/L rows per query, brute force about L library
+// points; measured on GB300 (N_m = 10^4, E = 1..10) the two cost the same at
+// L = 520..800, i.e. L ~ sqrt(48*N_m).  Below that brute force is faster.
+// The last term keeps R = 4(E+2)N_m/L + 64 within kTableMaxR.
+double table_min_L(int32_t E, int64_t n_m) {
+  return std::max({256.0, std::ceil(std::sqrt(48.0 * (double)n_m)),
+                   std::ceil(4.0 * (E + 2) * (double)n_m / (double)(kTableMaxR - 64))});
+}
 
 // Append the units of one problem.  Offsets: series block, first rho index.
 // Pairs that share a library variable j share one library and one neighbour
@@ -191,8 +212,8 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         ul->orders.push_back(oj);
       }
   // Distance indexing tables (CCM_TABLE): per (j, E, tau), realizations with
-  // L >= Ls read their neighbours from a table of the R nearest points of
-  // every query; R covers about four times the expected scan length
+  // L >= table_min_L read their neighbours from a table of the R nearest
+  // points of every query; R covers about four times the expected scan length
   // (E+2)*N_m/L at the smallest such L (CCM_TABLE_SAFETY changes the four).
   // A table is built only when the
   // realizations that use it would otherwise scan at least 8*N_m library
@@ -207,8 +228,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
       for (int32_t E : pc.E)
         for (int32_t tau : pc.tau) {
           const int64_t n_m = pc.n - (int64_t)(E - 1) * tau;
-          const double ls = std::max(256.0, std::ceil(4.0 * (E + 2) * (double)n_m /
-                                                       (double)(kTableMaxR - 64)));
+          const double ls = table_min_L(E, n_m);
           int64_t lmin = -1;
           double lsum = 0.0;
           for (int64_t L : pc.L)
@@ -217,7 +237,9 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
               lsum += (double)L * pc.r;
             }
           if (lmin < 0 || lsum < 8.0 * (double)n_m) continue;
-          int64_t R = (int64_t)std::ceil(safety * (E + 2) * (double)n_m / (double)lmin) + 64;
+          // the window removes up to 2W more of the nearest points from every row
+          int64_t R = (int64_t)std::ceil(safety * (E + 2) * (double)n_m / (double)lmin) + 64 +
+                      2 * (int64_t)pc.theiler;
           R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR), n_m);
           TableJob tj;
           std::memset(&tj, 0, sizeof(tj));
@@ -257,6 +279,8 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
             u.n_m = (int32_t)(pc.n - (int64_t)(E - 1) * tau);
             u.n_tiles = (u.n_m + tileq - 1) / tileq;
             u.n_targets = (int32_t)tp.size();
+            u.theiler = pc.theiler;
+            u.wfloor = pc.weight_floor;
             u.lib_off = ul->lib_total;
             u.part_off = ul->part_total;
             u.order_off = combo[std::make_tuple(j, E, tau)];
@@ -273,8 +297,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
               ul->targets.push_back(tg);
             }
             const auto tab = table_of.find(std::make_tuple(j, E, tau));
-            if (tab != table_of.end() && L >= 256 &&
-                (double)L >= std::ceil(4.0 * (E + 2) * (double)u.n_m / (double)(kTableMaxR - 64))) {
+            if (tab != table_of.end() && (double)L >= table_min_L(E, u.n_m)) {
               u.table_off = tab->second.first;
               u.table_R = tab->second.second;
             }
@@ -282,11 +305,14 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
             for (int32_t q = 0; q < u.n_tiles; ++q) {
               const int64_t nq = std::min<int64_t>(tileq, u.n_m - (int64_t)q * tileq);
               if (u.table_R > 0) {
-                // bitmap build, expected table scan, per-target epilogue
-                ul->items_table.push_back(WorkItem{uidx, q});
-                ul->item_cost_table.push_back((double)L + (double)nq * 12.0 * (E + 2) *
-                                              (double)u.n_m / (double)L +
-                                              (double)u.n_targets * nq * 64.0);
+                // one item per kTableChunk tiles: one bitmap build, then per
+                // tile the expected table scan and the per-target epilogue
+                if (q % kTableChunk == 0) {
+                  ul->items_table.push_back(WorkItem{uidx, q});
+                  ul->item_cost_table.push_back((double)L);
+                }
+                ul->item_cost_table.back() += (double)nq * 12.0 * (E + 2) * (double)u.n_m /
+                                              (double)L + (double)u.n_targets * nq * 64.0;
               } else {
                 ul->items.push_back(WorkItem{uidx, q});
                 // distance work, staging per library point, per-target epilogue

@@ -42,6 +42,8 @@ class Problem:
     r: int                       # realizations per (pair, E, tau, L) cell
     seed: int                    # library sampler seed
     name: str = ""
+    theiler: int = 0             # exclusion window W (0: only the query itself)
+    weight_floor: float = 0.0    # simplex weight floor f (0: none)
 
     @property
     def n_series(self) -> int:
@@ -230,4 +232,5 @@ def subproblem(p: Problem, pairs: Sequence[int] | None = None, E: Sequence[int] 
     pick = lambda arr, idx: arr if idx is None else np.ascontiguousarray(arr[list(idx)])
     return Problem(series=p.series, pairs=pick(p.pairs, pairs), E=pick(p.E, E),
                    tau=pick(p.tau, tau), L=pick(p.L, L), r=p.r if r is None else r,
-                   seed=p.seed, name=p.name + "-sub")
+                   seed=p.seed, name=p.name + "-sub", theiler=p.theiler,
+                   weight_floor=p.weight_floor)

@@ -63,7 +63,9 @@ def check_units(p, rho, lib, nbr, xh, which=None):
     for (u, j, i, E, tau, L, k, n_m, l_g, n_g, x_g) in split(p, lib, nbr, xh):
         if which is not None and u not in which:
             continue
-        r_o, l_o, n_o, x_o = oracle.ccm_unit(p.series, j, i, E, tau, L, k, p.seed, keep=True)
+        r_o, l_o, n_o, x_o = oracle.ccm_unit(p.series, j, i, E, tau, L, k, p.seed, keep=True,
+                                             theiler=getattr(p, "theiler", 0),
+                                             weight_floor=getattr(p, "weight_floor", 0.0))
         assert np.array_equal(l_g, l_o), f"library differs in unit {u}"
         assert np.array_equal(n_g, n_o), f"neighbours differ in unit {u} " \
             f"(first row {np.nonzero(np.any(n_g != n_o, axis=1))[0][:3]})"

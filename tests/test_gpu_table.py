@@ -64,7 +64,7 @@ def test_table_with_exact_ties_and_full_library(ccm):
     rng = np.random.default_rng(8)
     ints = rng.integers(0, 6, size=(2, 2500)).astype(np.float32)
     p = I.Problem(series=ints, pairs=I.BOTH_DIRECTIONS.copy(), E=np.array([1, 2, 3], np.int32),
-                  tau=np.array([1], np.int32), L=np.array([300, 2498], np.int64), r=8, seed=4,
+                  tau=np.array([1], np.int32), L=np.array([300, 2498], np.int64), r=10, seed=4,
                   name="ties")
     ctx = ccm.ccm_context_create(0)
     try:
@@ -84,24 +84,27 @@ def test_table_fallback_path(ccm, monkeypatch):
     base = I.sweep_problem()
     s = np.ascontiguousarray(base.series[:, :4000])
     p = I.Problem(series=s, pairs=I.BOTH_DIRECTIONS.copy(), E=np.array([3, 8], np.int32),
-                  tau=np.array([2], np.int32), L=np.array([400, 3000], np.int64), r=2,
+                  tau=np.array([2], np.int32), L=np.array([400, 3000], np.int64), r=12,
                   seed=base.seed, name="fallback")
     ctx = ccm.ccm_context_create(0)
     try:
+        assert uses_table(ccm, ctx, p)
         (r0, l0, n0, x0), (r1, l1, n1, x1) = both_paths(ccm, ctx, p)
     finally:
         ccm.ccm_context_destroy(ctx)
     assert np.array_equal(n0, n1) and np.array_equal(r0, r1)
 
 
-def test_table_fallback_small_e_regression(ccm):
-    """E = 2, tau = 3 on the full 10^4-point series: at L = 258 some queries
-    meet fewer than E+1 library members among their table entries and scan
-    their library; the scan must keep the whole sorted (distance, index) list."""
+def test_table_fallback_small_e_regression(ccm, monkeypatch):
+    """E = 2, tau = 3 on the full 10^4-point series with short table rows: at
+    L = 700 some queries meet fewer than E+1 library members among their
+    table entries and scan their library; the scan must keep the whole sorted
+    (distance, index) list."""
+    monkeypatch.setenv("CCM_TABLE_SAFETY", "0.05")
     base = I.sweep_problem()
     p = I.Problem(series=base.series, pairs=np.array([[1, 0]], np.int32),
                   E=np.array([2], np.int32), tau=np.array([3], np.int32),
-                  L=np.array([258, 9000], np.int64), r=29, seed=base.seed, name="fallback-e2")
+                  L=np.array([700, 9000], np.int64), r=29, seed=base.seed, name="fallback-e2")
     ctx = ccm.ccm_context_create(0)
     try:
         assert uses_table(ccm, ctx, p)
