@@ -88,6 +88,9 @@ def _load():
                                        ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, _F64P]
             lib.oracle_ccm.restype = ctypes.c_int
+            lib.oracle_convergence.argtypes = [_F64P, ctypes.c_int64, ctypes.c_int32, _I64P,
+                                               ctypes.c_int32, ctypes.c_double, _F64P]
+            lib.oracle_convergence.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -226,3 +229,21 @@ def ccm(series, pairs, E, tau, L, r: int, seed: int, select_fp64: bool = False,
     if rc != 0:
         raise ValueError("invalid CCM problem")
     return out
+
+
+def convergence(rho, L, z_crit: float = 1.6448536269514722) -> np.ndarray:
+    """Convergence decision per (pair, E, tau) row of rho [..., n_L, r]: an array
+    [..., 6] of (mean rho at the smallest L, at the largest L, Jonckheere-Terpstra
+    J, its z score, finite realizations, converged 0/1).  Default z_crit: the
+    one-sided 5% point of the standard normal."""
+    rho = _c(rho, np.float64)
+    L = _c(L, np.int64)
+    n_L, r = rho.shape[-2], rho.shape[-1]
+    assert len(L) == n_L
+    rows = rho.reshape(-1, n_L, r)
+    out = np.zeros((rows.shape[0], 6), np.float64)
+    rc = _load().oracle_convergence(_ptr(rows, _F64P), rows.shape[0], n_L, _ptr(L, _I64P), r,
+                                    float(z_crit), _ptr(out, _F64P))
+    if rc != 0:
+        raise ValueError("invalid convergence arguments")
+    return out.reshape(rho.shape[:-2] + (6,))

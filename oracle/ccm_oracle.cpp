@@ -238,6 +238,65 @@ void observed(const float* tgt_s, int64_t n, int32_t E, int32_t tau, double* x) 
   for (int64_t m = 0; m < n_m; ++m) x[m] = (double)tgt_s[m + (int64_t)(E - 1) * tau];
 }
 
+// ---------------------------------------------------------------------------
+// Convergence decision for one (pair, E, tau) row of the rho grid (Sect. 1:
+// skill should rise with L, judged over the r realizations; the paper states
+// no test, so this is a chosen reading).  Groups are the L values in
+// increasing order, each holding the finite rho of its realizations.  The
+// Jonckheere-Terpstra statistic counts, over every pair of groups a < b and
+// every pair of members (x in a, y in b), 1 when y > x and 1/2 when y == x.
+// With no trend (all rho exchangeable) and N = sum n_g:
+//   E[J]   = (N^2 - sum n_g^2) / 4,
+//   Var[J] = (N^2 (2N + 3) - sum n_g^2 (2 n_g + 3)) / 72   (no tie correction),
+//   z      = (J - E[J]) / sqrt(Var[J]).
+// The row converges when z > z_crit, the mean rho at the largest L exceeds
+// the mean at the smallest L, and the mean at the largest L is positive.
+// ---------------------------------------------------------------------------
+struct Convergence {
+  double rho_first, rho_last, jt, z;
+  int32_t n_valid, converged;
+};
+
+Convergence convergence_row(const double* row, int32_t n_L, const int64_t* L, int32_t r,
+                            double z_crit) {
+  std::vector<int32_t> order((size_t)n_L);
+  for (int32_t l = 0; l < n_L; ++l) order[(size_t)l] = l;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return L[a] < L[b]; });
+  std::vector<std::vector<double>> g((size_t)n_L);
+  for (int32_t q = 0; q < n_L; ++q) {
+    const double* x = row + (int64_t)order[(size_t)q] * r;
+    for (int32_t k = 0; k < r; ++k)
+      if (std::isfinite(x[k])) g[(size_t)q].push_back(x[k]);
+  }
+  Convergence c;
+  double J = 0.0, N = 0.0, S2 = 0.0, S3 = 0.0;
+  for (int32_t a = 0; a < n_L; ++a)
+    for (int32_t b = a + 1; b < n_L; ++b)
+      for (double x : g[(size_t)a])
+        for (double y : g[(size_t)b]) J += (y > x) ? 1.0 : (y == x ? 0.5 : 0.0);
+  for (int32_t a = 0; a < n_L; ++a) {
+    const double n = (double)g[(size_t)a].size();
+    N += n;
+    S2 += n * n;
+    S3 += n * n * (2.0 * n + 3.0);
+  }
+  const double mean = (N * N - S2) / 4.0;
+  const double var = (N * N * (2.0 * N + 3.0) - S3) / 72.0;
+  c.jt = J;
+  c.z = var > 0.0 ? (J - mean) / std::sqrt(var) : std::nan("");
+  auto avg = [](const std::vector<double>& v) {
+    double t = 0.0;
+    for (double x : v) t += x;
+    return v.empty() ? std::nan("") : t / (double)v.size();
+  };
+  c.rho_first = avg(g.front());
+  c.rho_last = avg(g.back());
+  c.n_valid = (int32_t)N;
+  c.converged = (c.z > z_crit && c.rho_last > c.rho_first && c.rho_last > 0.0) ? 1 : 0;
+  return c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -349,6 +408,24 @@ int oracle_ccm(const float* series, int32_t V, int64_t n, const int32_t* pairs, 
             if (rc != 0) return rc;
             ++o;
           }
+  return 0;
+}
+
+// Convergence decision for every (pair, E, tau) row of rho [rows][n_L][r]:
+// out[row*6 .. row*6+5] = rho_first, rho_last, J, z, n_valid, converged.
+int oracle_convergence(const double* rho, int64_t n_rows, int32_t n_L, const int64_t* L,
+                       int32_t r, double z_crit, double* out) {
+  if (n_rows < 0 || n_L < 2 || r < 1) return -1;
+  for (int64_t q = 0; q < n_rows; ++q) {
+    const Convergence c = convergence_row(rho + q * (int64_t)n_L * r, n_L, L, r, z_crit);
+    double* o = out + 6 * q;
+    o[0] = c.rho_first;
+    o[1] = c.rho_last;
+    o[2] = c.jt;
+    o[3] = c.z;
+    o[4] = (double)c.n_valid;
+    o[5] = (double)c.converged;
+  }
   return 0;
 }
 
