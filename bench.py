@@ -5,8 +5,10 @@ Workload (one "step"): the batched parameter sweep over a coupled logistic map
 of N=10^4 FP32 points: E=1..10, tau=1..4, 20 library sizes log-spaced 100..9000,
 r=250 realizations, both directions (800 cells x 250 x 2 = 4*10^5
 realizations, 4.0*10^9 neighbour queries, 8.45*10^12 query-library pairs).
-One step = one ccm_run of the whole sweep (library sampler + one persistent
-fused kNN/simplex/rho launch, replayed from a CUDA graph).
+One step = one ccm_run of the whole sweep (query order, library sampler and
+one persistent fused kNN/simplex/rho launch, replayed from a CUDA graph)
+followed by ccm_convergence, the per-(pair, E, tau) convergence decision on
+the rho grid.
 
 Prints one JSON line.  `value` is realizations/s with inputs resident on the
 device; `e2e` is the same metric through ccm_run with pinned host buffers
@@ -229,9 +231,12 @@ def run_ours(args, rank, world, local_rank):
     rho_dev = torch.zeros(ccm.rho_shape(p), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+    n_rows = len(p.pairs) * len(p.E) * len(p.tau)
+    conv_dev = torch.zeros(n_rows * 40, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
         ccm.ccm_run(plan, s_dev, rho_dev, stream=stream)
+        ccm.ccm_convergence(ctx, rho_dev, p.L, out=conv_dev, stream=stream)
         stream.synchronize()
 
     clocks = ClockSampler(local_rank)
@@ -239,17 +244,21 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, knn_ms, samp_ms = [], [], []
+    step_ms, knn_ms, samp_ms, conv_ms = [], [], [], []
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)
         e0 = torch.cuda.Event(enable_timing=True)
+        em = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ccm.ccm_run(plan, s_dev, rho_dev, stream=stream)
+        em.record(stream)
+        ccm.ccm_convergence(ctx, rho_dev, p.L, out=conv_dev, stream=stream)
         e1.record(stream)
         stream.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        conv_ms.append(em.elapsed_time(e1))
         a, b = ccm.ccm_plan_kernel_times(plan)
         samp_ms.append(a)
         knn_ms.append(b)
@@ -272,6 +281,7 @@ def run_ours(args, rank, world, local_rank):
         stream.synchronize()
         t0 = time.perf_counter()
         ccm.ccm_run(plan_h, s_host, rho_host)     # H2D, graph, D2H, synchronise
+        conv_host = ccm.ccm_convergence(ctx, rho_host, p.L)   # H2D, kernel, D2H
         e2e_s.append(time.perf_counter() - t0)
     e2e_t = reduce_max(sum(e2e_s) / len(e2e_s), dist, "cuda")
     same = bool(np.array_equal(rho_host, rho_dev.cpu().numpy()))
@@ -291,17 +301,22 @@ def run_ours(args, rank, world, local_rank):
                            parallelism="replicas" if world > 1 else "single GPU"),
             "queries_per_s": info["n_queries"] * world / (t_step / 1e3),
             "pairs_per_s": info["pair_count"] * world / (t_step / 1e3),
-            "kernel_ms": {"sampler": sum(samp_ms) / len(samp_ms), "knn_fused": knn},
+            "kernel_ms": {"sampler": sum(samp_ms) / len(samp_ms), "knn_fused": knn,
+                          "convergence": sum(conv_ms) / len(conv_ms)},
+            "convergence": {"rows": n_rows, "converged_rows": int(conv_host["converged"].sum()),
+                            "test": "one-sided Jonckheere-Terpstra over the 20 L groups, "
+                                    "z > 1.645"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic_entry(),
                          "kernel": "knn_fused (3E FP32 flops per query-library pair)",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "e2e": {"value": job_throughput(n_units, world, e2e_t), "unit": UNIT,
-                    "h2d_bytes_per_step": int(p.series.nbytes),
-                    "d2h_bytes_per_step": int(rho_host.nbytes),
+                    "h2d_bytes_per_step": int(p.series.nbytes) + int(rho_host.nbytes),
+                    "d2h_bytes_per_step": int(rho_host.nbytes) + int(conv_host.nbytes),
                     "ms_per_step": e2e_t * 1e3, "same_rho_as_device_path": same},
-            "gpu_launches": 2 * args.steps,
+            # per step: query order, sampler, fused kNN, convergence
+            "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "rho_finite": rho_ok,
         }

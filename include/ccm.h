@@ -221,6 +221,33 @@ ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, int64_t n, i
                            int32_t i, int32_t E, int32_t tau, int64_t L, int32_t r,
                            uint64_t seed, double* d_rho, void* cuda_stream);
 
+/* Convergence decision for one (pair, E, tau) row of the rho grid. */
+typedef struct {
+  double rho_first;   /* mean rho of the finite realizations at the smallest L */
+  double rho_last;    /* the same at the largest L */
+  double jt;          /* Jonckheere-Terpstra J over the L groups in increasing L:
+                         pairs (x earlier, y later) with y > x count 1, y == x 1/2 */
+  double z;           /* (J - E[J]) / sqrt(Var[J]) with no trend, no tie correction:
+                         E[J] = (N^2 - sum n_g^2)/4,
+                         Var[J] = (N^2(2N+3) - sum n_g^2(2n_g+3))/72, N = sum n_g */
+  int32_t n_valid;    /* finite realizations in the row (N) */
+  int32_t converged;  /* 1 when z > z_crit, rho_last > rho_first and rho_last > 0 */
+} ccm_convergence_t;
+
+/* Convergence of cross-map skill with L (paper Sect. 1: skill should rise with
+ * the library size, judged over the r realizations; the paper states no test,
+ * this one-sided trend test is the reading taken).  rho: [n_rows][n_L][r] FP64,
+ * the layout ccm_run writes (n_rows = n_pairs*n_E*n_tau); L: host [n_L], the
+ * grid's library sizes in the order of rho's L axis (any order, distinct).
+ * Non-finite rho are left out.  out: [n_rows].  flags: CCM_INPUT_ON_DEVICE
+ * (rho is device memory), CCM_OUTPUT_ON_DEVICE (out is device memory); host
+ * buffers are staged through temporary device memory.  Limits: 2 <= n_L <= 64,
+ * n_L*r <= 24576.  cuda_stream as in ccm_run (NULL: blocks until done).
+ * Results equal the oracle's bit for bit (exact integer J, fixed FP64 order). */
+ccm_status ccm_convergence(ccm_context* ctx, const double* rho, int64_t n_rows, int32_t n_L,
+                           const int64_t* L, int32_t r, double z_crit,
+                           ccm_convergence_t* out, uint32_t flags, void* cuda_stream);
+
 /* Thread-local message describing the last non-OK status on this thread. */
 const char* ccm_last_error(void);
 

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libccm_gb300.so")
 SOURCES = ["runtime.cu", "sampler.cu", "knn_fused.cu", "plain.cu", "noalloc.cu", "order.cu",
-           "table.cu"]
+           "table.cu", "convergence.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

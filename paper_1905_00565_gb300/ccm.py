@@ -44,7 +44,8 @@ STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM
 EXPORTED = ["ccm_context_create", "ccm_context_destroy", "ccm_plan", "ccm_plan_destroy",
             "ccm_plan_get_info", "ccm_run", "ccm_run_ex", "ccm_run_plain", "ccm_submit",
             "ccm_poll", "ccm_cancel", "ccm_job_times", "ccm_last_error", "ccm_version",
-            "ccm_plan_kernel_times", "ccm_run_noalloc", "ccm_plan_stage_times"]
+            "ccm_plan_kernel_times", "ccm_run_noalloc", "ccm_plan_stage_times",
+            "ccm_convergence"]
 
 
 class ccm_problem(ctypes.Structure):
@@ -101,6 +102,8 @@ def _load():
         "ccm_job_times": ([vp, u64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], st),
         "ccm_run_noalloc": ([vp, i32, i64, i32, i32, i32, i32, i64, i32, u64, vp, vp], st),
+        "ccm_convergence": ([vp, vp, i64, i32, vp, i32, ctypes.c_double, vp, ctypes.c_uint32,
+                             vp], st),
         "ccm_last_error": ([], ctypes.c_char_p),
         "ccm_version": ([], ctypes.c_char_p),
     }
@@ -274,3 +277,40 @@ def plan_problem(ctx: int, problem, flags: int = 0) -> int:
 
 def rho_shape(problem) -> tuple:
     return (len(problem.pairs), len(problem.E), len(problem.tau), len(problem.L), int(problem.r))
+
+
+CONVERGENCE_FIELDS = ("rho_first", "rho_last", "jt", "z", "n_valid", "converged")
+
+
+class ccm_convergence_t(ctypes.Structure):
+    _fields_ = [("rho_first", ctypes.c_double), ("rho_last", ctypes.c_double),
+                ("jt", ctypes.c_double), ("z", ctypes.c_double),
+                ("n_valid", ctypes.c_int32), ("converged", ctypes.c_int32)]
+
+
+_CONV_DTYPE = np.dtype([("rho_first", "<f8"), ("rho_last", "<f8"), ("jt", "<f8"), ("z", "<f8"),
+                        ("n_valid", "<i4"), ("converged", "<i4")])
+
+
+def ccm_convergence(ctx: int, rho, L, z_crit: float = 1.6448536269514722, out=None,
+                    stream=None):
+    """Convergence decision per (pair, E, tau) row of ``rho`` [..., n_L, r] (host
+    numpy or device tensor).  Returns a structured numpy array [...] with the
+    fields of ccm_convergence_t, or fills ``out`` (device memory of 40 bytes
+    per row, e.g. a uint8 tensor) and returns it."""
+    L = np.ascontiguousarray(np.asarray(L, np.int64).reshape(-1))
+    shape = tuple(rho.shape)
+    n_L, r = int(shape[-2]), int(shape[-1])
+    if len(L) != n_L:
+        raise ValueError("L must match rho's L axis")
+    n_rows = int(np.prod(shape[:-2])) if len(shape) > 2 else 1
+    on_dev = not isinstance(rho, np.ndarray)
+    flags = CCM_INPUT_ON_DEVICE if on_dev else 0
+    if out is None:
+        host = np.zeros(n_rows, _CONV_DTYPE)
+        _check(_lib.ccm_convergence(ctx, _ptr(rho), n_rows, n_L, L.ctypes.data, r,
+                                    float(z_crit), host.ctypes.data, flags, _stream(stream)))
+        return host.reshape(shape[:-2])
+    _check(_lib.ccm_convergence(ctx, _ptr(rho), n_rows, n_L, L.ctypes.data, r, float(z_crit),
+                                _ptr(out), flags | CCM_OUTPUT_ON_DEVICE, _stream(stream)))
+    return out

@@ -147,6 +147,21 @@ cudaError_t launch_knn_table(const KnnParams& p, int max_nm, int grid, cudaStrea
 void set_last_error(const char* msg);
 
 // Plain comparator (plain.cu): one realization per call.
+// Convergence decision (one CTA per (pair, E, tau) row of the rho grid).
+constexpr int kMaxConvGroups = 64;      // L values per row, at most
+constexpr int kMaxConvValues = 24576;   // n_L * r per row, at most (shared memory)
+struct ConvOrder {
+  int32_t group[kMaxConvGroups];        // L-axis index of the g-th smallest L
+};
+struct ConvergenceRow {                 // same layout as ccm_convergence_t
+  double rho_first, rho_last, jt, z;
+  int32_t n_valid, converged;
+};
+cudaError_t convergence_prepare();
+cudaError_t launch_convergence(const double* rho, int64_t n_rows, int32_t n_L, int32_t r,
+                               const ConvOrder& ord, double z_crit, ConvergenceRow* out,
+                               cudaStream_t s);
+
 cudaError_t launch_plain_unit(const float* series, const UnitDesc* unit_dev, const UnitDesc& unit,
                               const TargetDesc* target_dev, const int32_t* lib,
                               float* xhat_scratch, double* rho_out, cudaStream_t s);

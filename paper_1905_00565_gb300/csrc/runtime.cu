@@ -770,6 +770,7 @@ ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context**
   CCM_CUDA(knn_prepare());
   CCM_CUDA(order_prepare());
   CCM_CUDA(table_prepare());
+  CCM_CUDA(convergence_prepare());
   size_t free_b = 0, total_b = 0;
   CCM_CUDA(cudaMemGetInfo(&free_b, &total_b));
   std::unique_ptr<ccm_context> ctx(new ccm_context());
@@ -1015,6 +1016,55 @@ ccm_status ccm_run_plain(ccm_plan_t* plan, const float* series, double* rho, voi
   CCM_CUDA(cudaMemcpyAsync(rho, base + ar.rho, sizeof(double) * (size_t)plan->ul.n_rho,
                            out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   if (!cuda_stream || !in_dev || !out_dev) return check_err_flag(base, ar, s);
+  return CCM_OK;
+}
+
+ccm_status ccm_convergence(ccm_context* ctx, const double* rho, int64_t n_rows, int32_t n_L,
+                           const int64_t* L, int32_t r, double z_crit,
+                           ccm_convergence_t* out, uint32_t flags, void* cuda_stream) {
+  static_assert(sizeof(ConvergenceRow) == sizeof(ccm_convergence_t), "layout");
+  if (!ctx || !rho || !L || !out) return fail(CCM_EINVAL, "NULL argument");
+  if (n_rows < 0 || n_rows > 0x7fffffff) return fail(CCM_EINVAL, "n_rows out of range");
+  if (n_L < 2 || n_L > kMaxConvGroups) return fail(CCM_EINVAL, "n_L must be in 2..64");
+  if (r < 1 || (int64_t)n_L * r > kMaxConvValues)
+    return fail(CCM_EINVAL, "need r >= 1 and n_L*r <= 24576");
+  if (std::isnan(z_crit)) return fail(CCM_EINVAL, "z_crit is NaN");
+  ConvOrder ord;
+  std::memset(&ord, 0, sizeof(ord));
+  for (int32_t g = 0; g < n_L; ++g) ord.group[g] = g;
+  std::stable_sort(ord.group, ord.group + n_L, [&](int32_t a, int32_t b) { return L[a] < L[b]; });
+  for (int32_t g = 1; g < n_L; ++g)
+    if (L[ord.group[g]] == L[ord.group[g - 1]]) return fail(CCM_EINVAL, "L values must differ");
+  if (n_rows == 0) return CCM_OK;
+  CCM_CUDA(cudaSetDevice(ctx->device));
+  const bool in_dev = (flags & CCM_INPUT_ON_DEVICE) != 0;
+  const bool out_dev = (flags & CCM_OUTPUT_ON_DEVICE) != 0;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t rho_bytes = sizeof(double) * (size_t)n_rows * (size_t)n_L * (size_t)r;
+  const size_t out_bytes = sizeof(ccm_convergence_t) * (size_t)n_rows;
+  double* d_rho = const_cast<double*>(rho);
+  ConvergenceRow* d_out = reinterpret_cast<ConvergenceRow*>(out);
+  void* tmp = nullptr;
+  if (!in_dev || !out_dev) {
+    CCM_CUDA(cudaMalloc(&tmp, (in_dev ? 0 : rho_bytes + 256) + (out_dev ? 0 : out_bytes)));
+    char* t = static_cast<char*>(tmp);
+    if (!in_dev) {
+      d_rho = reinterpret_cast<double*>(t);
+      t += (rho_bytes + 255) / 256 * 256;
+    }
+    if (!out_dev) d_out = reinterpret_cast<ConvergenceRow*>(t);
+  }
+  cudaError_t e = cudaSuccess;
+  if (!in_dev) e = cudaMemcpyAsync(d_rho, rho, rho_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_convergence(d_rho, n_rows, n_L, r, ord, z_crit, d_out, s);
+  if (e == cudaSuccess && !out_dev)
+    e = cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && (tmp || !cuda_stream)) e = cudaStreamSynchronize(s);
+  if (tmp) {
+    const cudaError_t e2 = cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return fail(CCM_ECUDA, std::string("ccm_convergence: ") + cudaGetErrorString(e));
   return CCM_OK;
 }
 
