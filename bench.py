@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=40)
+    ap.add_argument("--scenario", default="", choices=["", "paper"],
+                    help="paper: the paper's baseline scenario and its one-at-a-time "
+                         "elasticity cases (context, not the bench line)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run every sweep cell with R realizations through ccm_run "
                          "twice (the small case for ncu captures) and exit")
@@ -468,10 +471,83 @@ def profile_case(r: int):
     ccm.ccm_context_destroy(ctx)
 
 
+def paper_scenario(args):
+    """The paper's baseline scenario (N=4000, r=500, L in {500,1000,2000}, E and
+    tau in {1,2,4}) and its elasticity cases (one of L, E, tau fixed to each of
+    its three values, the others as in the baseline), on the GPU with brute
+    force and with distance indexing tables, and on one host core with the
+    oracle (a seeded sample of 2 realizations per cell, scaled to r=500).
+    Prints one JSON line of times and doubling ratios; the paper's ratios
+    (Spark, unnamed series) are quoted beside them as context."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1905_00565_gb300 import ccm
+    from paper_1905_00565_gb300 import inputs as I
+
+    base = I.paper_scenario_problem()
+    cases = {"baseline": base}
+    for axis in ("L", "E", "tau"):
+        for q in range(3):
+            cases[f"{axis}={int(getattr(base, axis)[q])}"] = I.subproblem(base, **{axis: [q]})
+    ctx = ccm.ccm_context_create(0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s_dev = torch.from_numpy(base.series).cuda()
+    dev = ccm.CCM_INPUT_ON_DEVICE | ccm.CCM_OUTPUT_ON_DEVICE
+    res = {}
+    for name, p in cases.items():
+        row = {"realizations": p.n_units()}
+        for label, flags in (("gpu_ms", dev), ("gpu_table_ms", dev | ccm.CCM_TABLE)):
+            plan = ccm.plan_problem(ctx, p, flags)
+            rho = torch.zeros(ccm.rho_shape(p), dtype=torch.float64, device="cuda")
+            for _ in range(max(3, args.warmup)):
+                ccm.ccm_run(plan, s_dev, rho, stream=stream)
+            ts = []
+            for k in range(max(5, args.steps)):
+                with torch.cuda.stream(stream):
+                    flush.fill_(k & 0xFF)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ccm.ccm_run(plan, s_dev, rho, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            row[label] = statistics.median(ts)
+            ccm.ccm_plan_destroy(plan)
+        sub = I.subproblem(p, r=2)
+        t0 = time.perf_counter()
+        oracle.ccm(sub.series, sub.pairs, sub.E, sub.tau, sub.L, sub.r, sub.seed)
+        row["oracle_1core_s"] = (time.perf_counter() - t0) * p.r / sub.r
+        res[name] = row
+    ccm.ccm_context_destroy(ctx)
+
+    def ratios(axis, key):
+        vals = [res[f"{axis}={int(v)}"][key] for v in getattr(base, axis)]
+        return [vals[1] / vals[0], vals[2] / vals[1]]
+
+    out = {"scenario": "paper baseline and elasticity (Table 2) on a synthetic stand-in",
+           "workload": "coupled logistic map N=4000, both directions, r=500, "
+                       "L in {500,1000,2000}, E and tau in {1,2,4}",
+           "cases": res,
+           "doubling_ratios": {f"{axis}": {k: ratios(axis, k) for k in
+                                           ("gpu_ms", "gpu_table_ms", "oracle_1core_s")}
+                               for axis in ("L", "E", "tau")},
+           "paper_context": {"L_doubling_single_threaded": 4.06, "L_doubling_parallel": 1.11,
+                             "tau_doubling_single_threaded": 1.13,
+                             "E_or_tau_doubling_parallel": "almost no impact",
+                             "hardware": "Spark on YARN, 1 master + 5 workers, 4 cores each"}}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.scenario == "paper":
+        paper_scenario(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -76,8 +76,9 @@ constexpr int kTableChunk = 8;         // query tiles per table work item (one b
 struct SamplerParams {
   const UnitDesc* units;
   const TargetDesc* targets;  // for the debug copies (lib_dbg_off per target)
-  int32_t* lib;           // library buffer (sum of L)
-  int32_t* dbg_lib;       // optional: libraries again, once per target, in rho order
+  const int32_t* order;   // query orders (per variable, E, tau); libraries follow them
+  int32_t* lib;           // library buffer (sum of L), each library in query order
+  int32_t* dbg_lib;       // optional: libraries in ascending m, once per target, in rho order
   int32_t* err;           // error flag (set, never cleared, by the kernels)
 };
 
@@ -135,8 +136,8 @@ int knn_block_threads();
 int knn_queries_per_thread();
 size_t knn_smem_bytes(int emin, int emax);
 cudaError_t knn_prepare();
-cudaError_t knn_occupancy(int emin, int emax, int* ctas_per_sm);
-cudaError_t launch_knn(const KnnParams& p, int emin, int emax, int grid, cudaStream_t s);
+cudaError_t knn_occupancy(int E, int* ctas_per_sm);
+cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s);
 // Table path: same work items, neighbours read from the distance indexing table.
 size_t knn_table_smem(int max_nm);
 cudaError_t knn_table_prepare(int max_nm);

@@ -46,14 +46,17 @@ using u64 = unsigned long long;
 constexpr int kThreads = 256;             // threads per CTA = queries per tile
 constexpr int kQT = kThreads;             // queries per tile (one per thread)
 constexpr int kBuf = 16;                  // pending candidates per query
-constexpr int kCoordBytes = 40 * 1024;    // shared memory for one library tile
+constexpr int kCoordBytes = 40 * 1024;    // shared memory for one library tile + chunk boxes
+constexpr int kBoxBytes = 2 * 1024;       // chunk bounding boxes, at the end of that region
+constexpr int kChunk = 32;                // library points per bounding box
 constexpr int kBufBytes = kBuf * kThreads * 8;
 constexpr int kSmemBytes = kCoordBytes + kBufBytes;
 constexpr unsigned kFull = 0xffffffffu;
 // Kernel variants picked per E by the autotuner (results are identical):
 //   V = 0 "narrow": 4 library points per step, no early termination;
-//   V = 1 "wide":   8 points per step and, for E = 3..6, early termination
-//                   (E <= 6 only: above, registers run out and the two coincide).
+//   V = 1 "wide":   early termination for E >= 3 (after 2 coordinates for
+//                   E <= 6, after 3 above), and 8 points per step for E <= 6
+//                   (4 above: registers run out).
 constexpr int kVariants = 2;
 
 // Library points per step (two points per packed operand): more points give
@@ -63,14 +66,16 @@ constexpr int kStepE = (V == 1 && E <= 6) ? 8 : 4;
 
 // Coordinates summed before the early-termination check (E when there is none).
 template <int E, int V>
-constexpr int kE1 = (V == 1 && E >= 3 && E <= 6) ? 2 : E;
+constexpr int kE1 = (V == 1 && E >= 3) ? (E <= 6 ? 2 : 3) : E;
 
 template <int E>
 struct TileShape {
   static constexpr int EP = E + (E & 1);                        // coordinates padded to even
+  static constexpr int D = E < 3 ? E : 3;                       // coordinates a chunk box bounds
   // library points per tile: a point pair takes EP*8 bytes of coordinates + 8 of indices
-  static constexpr int LT = (kCoordBytes / (EP * 8 + 8)) * 2 / 64 * 64;
-  static_assert(LT >= 64 && LT % 8 == 0, "tile must hold whole steps");
+  static constexpr int LT = ((kCoordBytes - kBoxBytes) / (EP * 8 + 8)) * 2 / 64 * 64;
+  static_assert(LT >= 64 && LT % kChunk == 0, "tile must hold whole chunks");
+  static_assert((LT / kChunk) * 2 * D * 4 <= kBoxBytes, "chunk boxes must fit");
 };
 
 __device__ __forceinline__ u64 pack2(float a, float b) {
@@ -138,21 +143,29 @@ __device__ __forceinline__ float min_all(const float (&d)[N]) {
   return m;
 }
 
-// Insert (x, lx) into the ascending list kd[0..K), keeping entries that are
-// equal to x ahead of it (they arrived earlier, with smaller index).  A no-op
-// when x is not below kd[K-1].
+// The selection key: (squared distance, manifold index), lexicographic.
+__device__ __forceinline__ bool key_less(float d, int l, float kd, int kl) {
+  return d < kd || (d == kd && l < kl);
+}
+
+// The same key packed in 64 bits: the bits of a non-negative float order
+// like its value, so (bits << 32 | index) compares like (d, index).
+__device__ __forceinline__ u64 pack_key(float d, int l) {
+  return ((u64)__float_as_uint(d) << 32) | (u64)(uint32_t)l;
+}
+__device__ __forceinline__ float key_dist(u64 k) { return __uint_as_float((uint32_t)(k >> 32)); }
+__device__ __forceinline__ int key_index(u64 k) { return (int)(uint32_t)k; }
+
+// Insert key x into the ascending list ku[0..K); a no-op when x is not below
+// the last entry.  The library is visited in any order.
 template <int K>
-__device__ __forceinline__ void insert_sorted(float (&kd)[K], int (&kl)[K], float x, int lx) {
+__device__ __forceinline__ void insert_sorted(u64 (&ku)[K], u64 x) {
   bool below[K];
 #pragma unroll
-  for (int s = 0; s < K; ++s) below[s] = x < kd[s];
+  for (int s = 0; s < K; ++s) below[s] = x < ku[s];
 #pragma unroll
-  for (int s = K - 1; s > 0; --s) {
-    kd[s] = below[s - 1] ? kd[s - 1] : (below[s] ? x : kd[s]);
-    kl[s] = below[s - 1] ? kl[s - 1] : (below[s] ? lx : kl[s]);
-  }
-  kd[0] = below[0] ? x : kd[0];
-  kl[0] = below[0] ? lx : kl[0];
+  for (int s = K - 1; s > 0; --s) ku[s] = below[s - 1] ? ku[s - 1] : (below[s] ? x : ku[s]);
+  ku[0] = below[0] ? x : ku[0];
 }
 
 // Butterfly sum over the warp: every lane ends with the same bits (each
@@ -326,11 +339,13 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   constexpr int K = E + 1;  // the window keeps m itself out, so E+1 slots suffice
   constexpr int EP = TileShape<E>::EP;
   constexpr int LT = TileShape<E>::LT;
+  constexpr int D = TileShape<E>::D;
   u64* s_coord = reinterpret_cast<u64*>(smem);                                   // [LT/2][EP]
   int32_t* s_lidx = reinterpret_cast<int32_t*>(smem + (size_t)(LT / 2) * EP * 8);  // [LT]
-  int2* s_buf = reinterpret_cast<int2*>(smem + kCoordBytes);                     // [kBuf][kThreads]
+  float* s_box = reinterpret_cast<float*>(smem + kCoordBytes - kBoxBytes);       // [LT/32][2D]
+  u64* s_buf = reinterpret_cast<u64*>(smem + kCoordBytes);                      // [kBuf][kThreads]
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int n_m = u.n_m, L = u.L, tau = u.tau, W = u.theiler;
   const int off = (E - 1) * tau;
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
@@ -351,77 +366,134 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
     const float c = sj[m + off - e * tau];
     qc[e] = pack2(c, c);
   }
-
-  float kd[K];
-  int kl[K];
+  // Bounding box of the warp's queries over the first D coordinates.
+  float qlo[D], qhi[D];
 #pragma unroll
-  for (int s = 0; s < K; ++s) {
-    kd[s] = INFINITY;
-    kl[s] = -1;
+  for (int e = 0; e < D; ++e) {
+    float lo = sj[m + off - e * tau], hi = lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    qlo[e] = lo;
+    qhi[e] = hi;
   }
+
+  u64 ku[K];  // the E+1 smallest keys so far, ascending
+#pragma unroll
+  for (int s = 0; s < K; ++s) ku[s] = pack_key(INFINITY, INT_MAX);
   int cnt = 0;
 
   auto merge_all = [&]() {
     const int mx = (int)__reduce_max_sync(kFull, (unsigned)cnt);
-    for (int b = 0; b < mx; ++b) {
-      if (b < cnt) {
-        const int2 v = s_buf[b * kThreads + tid];
-        insert_sorted<K>(kd, kl, __int_as_float(v.x), v.y);
-      }
-    }
+    for (int b = 0; b < mx; ++b)
+      if (b < cnt) insert_sorted<K>(ku, s_buf[b * kThreads + tid]);
     cnt = 0;
   };
 
+  // The library is stored in query order, so a run of it sits near this
+  // tile's queries: start there (wrapping around) so that the thresholds are
+  // tight from the first chunks on.
+  const int a0 = (int)((int64_t)L * (int64_t)(tile * kQT) / n_m);
   for (int t0 = 0; t0 < L; t0 += LT) {
     const int nt = min(LT, L - t0);
-    const int ntp = (nt + kStep - 1) / kStep * kStep;
+    const int ntp = (nt + kChunk - 1) / kChunk * kChunk;
     __syncthreads();  // the previous tile has been consumed
-    for (int a = tid; a < ntp; a += kThreads) {
+    for (int a = tid; a < ntp; a += kThreads) {  // a warp stages one chunk
       const int pp = a >> 1, half = a & 1;
       float* cpair = reinterpret_cast<float*>(s_coord + (size_t)pp * EP);
+      float c0[D];
       if (a < nt) {
-        const int l = lib[t0 + a];
+        int g = a0 + t0 + a;
+        g -= (g >= L) ? L : 0;
+        const int l = lib[g];
         s_lidx[a] = l;
 #pragma unroll
-        for (int e = 0; e < E; ++e) cpair[2 * e + half] = sj[l + off - e * tau];
+        for (int e = 0; e < E; ++e) {
+          const float c = sj[l + off - e * tau];
+          cpair[2 * e + half] = c;
+          if (e < D) c0[e] = c;
+        }
       } else {  // sentinel point: infinite distance, never selected
-        s_lidx[a] = 0x7fffffff;
+        s_lidx[a] = INT_MAX;
 #pragma unroll
         for (int e = 0; e < E; ++e) cpair[2 * e + half] = INFINITY;
+#pragma unroll
+        for (int e = 0; e < D; ++e) c0[e] = INFINITY;
       }
       if (EP > E) cpair[2 * E + half] = 0.f;
+      // chunk box over the first D coordinates (sentinels widen only hi)
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        float lo = c0[e], hi = c0[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+          hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+        if (lane == 0) {
+          s_box[(a >> 5) * 2 * D + e] = lo;
+          s_box[(a >> 5) * 2 * D + D + e] = hi;
+        }
+      }
     }
     __syncthreads();
 
 #pragma unroll 1
     for (int a = 0; a < ntp; a += kStep) {
+      if ((a & (kChunk - 1)) == 0) {
+        // Chunk pruning.  gap_e = max(0, lo_e - qhi_e, qlo_e - hi_e) bounds
+        // |q_e - x_e| from below for every query q of the warp and point x of
+        // the chunk, in FP32 too (rounding is monotone); summed in the
+        // distance's own order over the first D coordinates it bounds every
+        // FP32 squared distance between them from below.  A chunk whose bound
+        // exceeds every lane's threshold holds no candidate.
+        const float* bx = s_box + (a >> 5) * 2 * D;
+        float lb = 0.f;
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+          const float g = fmaxf(fmaxf(__fsub_rn(bx[e], qhi[e]), __fsub_rn(qlo[e], bx[D + e])), 0.f);
+          lb = (e == 0) ? __fmul_rn(g, g) : __fmaf_rn(g, g, lb);
+        }
+        const float th_max =
+            __uint_as_float(__reduce_max_sync(kFull, (uint32_t)(ku[K - 1] >> 32)));
+        if (lb > th_max) {
+          a += kChunk - kStep;
+          continue;
+        }
+      }
       const u64* cp = s_coord + (size_t)(a >> 1) * EP;
       // Partial sums over the first E1 coordinates are lower bounds of the
       // full FP32 sums (all terms are >= 0 and rounding is monotone), so a
-      // step whose partials are all at or above every lane's threshold cannot
+      // step whose partials are all above every lane's threshold cannot
       // contribute a candidate and skips the remaining coordinates.
       u64 r[kPairs];
 #pragma unroll
       for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, (kE1<E, V>)>(qc, cp + pp * EP, 0ull);
-      const float th = kd[K - 1];
+      const float th = key_dist(ku[K - 1]);
       float d[kStep];
 #pragma unroll
       for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
-      if (!__any_sync(kFull, min_all(d) < th)) continue;
+      if (!__any_sync(kFull, min_all(d) <= th)) continue;
       if constexpr ((kE1<E, V>) < E) {
 #pragma unroll
         for (int pp = 0; pp < kPairs; ++pp) {
           r[pp] = sqdist2_range<E, (kE1<E, V>), E>(qc, cp + pp * EP, r[pp]);
           unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
         }
-        if (!__any_sync(kFull, min_all(d) < th)) continue;
+        if (!__any_sync(kFull, min_all(d) <= th)) continue;
       }
+      const u64 thk = ku[K - 1];
 #pragma unroll
       for (int pt = 0; pt < kStep; ++pt) {
-        if (d[pt] < th) {
+        if (d[pt] <= th) {
           const int l = s_lidx[a + pt];
-          if (abs(l - m) > W) {  // exclusion window; W = 0 drops only m itself
-            s_buf[cnt * kThreads + tid] = make_int2(__float_as_int(d[pt]), l);
+          const u64 key = pack_key(d[pt], l);
+          // below the current last entry, outside the exclusion window
+          // (W = 0 drops only m itself)
+          if (key < thk && abs(l - m) > W) {
+            s_buf[cnt * kThreads + tid] = key;
             ++cnt;
           }
         }
@@ -437,8 +509,8 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   int nb[E + 1];
 #pragma unroll
   for (int s = 0; s <= E; ++s) {
-    dd[s] = kd[s];
-    nb[s] = kl[s];
+    dd[s] = key_dist(ku[s]);
+    nb[s] = key_index(ku[s]);
   }
   // the library tile in shared memory is free once every thread is in the epilogue
   finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, reinterpret_cast<double*>(smem), s_last);
@@ -532,22 +604,21 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
       for (int s2 = 0; s2 <= E; ++s2) nb[s2] = valid ? s_hit[s2 * kThreads + tid] : 0;
     } else {
       // Rare: fewer than E+1 members among the R nearest points; scan the
-      // library (ascending index; the strict "<" keeps equal distances in
-      // index order).
+      // library, keeping the E+1 smallest (distance, index) keys.
       float kd[E + 1];
       int kl[E + 1];
 #pragma unroll
       for (int s2 = 0; s2 <= E; ++s2) {
         kd[s2] = INFINITY;
-        kl[s2] = -1;
+        kl[s2] = INT_MAX;
       }
       for (int a = 0; a < L; ++a) {
         const int l = lib[a];
         if (abs(l - m) <= W) continue;
         const float d = d2_point<E>(sj, off, tau, q, l);
-        if (d < kd[E]) {
+        if (key_less(d, l, kd[E], kl[E])) {
           int s2 = E;
-          while (s2 > 0 && d < kd[s2 - 1]) {
+          while (s2 > 0 && key_less(d, l, kd[s2 - 1], kl[s2 - 1])) {
             kd[s2] = kd[s2 - 1];
             kl[s2] = kl[s2 - 1];
             --s2;
@@ -592,31 +663,7 @@ __global__ void __launch_bounds__(kThreads, 3) knn_table_kernel(KnnParams p) {
   }
 }
 
-template <int EMIN, int EMAX>
-__device__ __forceinline__ bool dispatch(int E, const KnnParams& p, const UnitDesc& u, int unit,
-                                         int tile, unsigned char* smem, int* s_last) {
-  bool ok = false;
-#define CCM_CASE(EV)                                                    \
-  if constexpr (EV >= EMIN && EV <= EMAX) {                             \
-    if (E == EV) {                                                      \
-      if constexpr (EV <= 6) {                                          \
-        if (p.variant[EV] == 1)                                         \
-          process_tile<EV, 1>(p, u, unit, tile, smem, s_last);          \
-        else                                                            \
-          process_tile<EV, 0>(p, u, unit, tile, smem, s_last);          \
-      } else {                                                          \
-        process_tile<EV, 0>(p, u, unit, tile, smem, s_last);            \
-      }                                                                 \
-      ok = true;                                                        \
-    }                                                                   \
-  }
-  CCM_CASE(1) CCM_CASE(2) CCM_CASE(3) CCM_CASE(4) CCM_CASE(5)
-  CCM_CASE(6) CCM_CASE(7) CCM_CASE(8) CCM_CASE(9) CCM_CASE(10)
-#undef CCM_CASE
-  return ok;
-}
-
-template <int EMIN, int EMAX>
+template <int E>
 __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item, s_last;
@@ -630,28 +677,15 @@ __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
     if ((int64_t)it >= p.n_items) break;
     const WorkItem w = p.items[it];
     const UnitDesc u = p.units[w.unit];
-    if (!dispatch<EMIN, EMAX>(u.E, p, u, w.unit, w.tile, smem, &s_last)) {
+    if (u.E != E) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
+      continue;
     }
+    if (p.variant[E] == 1)
+      process_tile<E, 1>(p, u, w.unit, w.tile, smem, &s_last);
+    else
+      process_tile<E, 0>(p, u, w.unit, w.tile, smem, &s_last);
   }
-}
-
-template <int EMIN, int EMAX>
-cudaError_t launch_range(const KnnParams& p, int grid, cudaStream_t s) {
-  knn_fused_kernel<EMIN, EMAX><<<grid, kThreads, kSmemBytes, s>>>(p);
-  return cudaGetLastError();
-}
-
-template <int EMIN, int EMAX>
-cudaError_t prepare_range() {
-  return cudaFuncSetAttribute(knn_fused_kernel<EMIN, EMAX>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-}
-
-template <int EMIN, int EMAX>
-cudaError_t occupancy_range(int* ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_fused_kernel<EMIN, EMAX>,
-                                                       kThreads, kSmemBytes);
 }
 
 }  // namespace
@@ -679,37 +713,39 @@ cudaError_t launch_knn_table(const KnnParams& p, int max_nm, int grid, cudaStrea
 int knn_queries_per_thread() { return 1; }
 size_t knn_smem_bytes(int, int) { return kSmemBytes; }
 
-// Instantiations: one kernel per single E (used when a plan has one E) and
-// one for the whole range 1..10 (mixed sweeps).
-#define CCM_FOR_RANGES(X) \
-  X(1, 1) X(2, 2) X(3, 3) X(4, 4) X(5, 5) X(6, 6) X(7, 7) X(8, 8) X(9, 9) X(10, 10) X(1, 10)
+// One kernel per E (each keeps all its registers for that E's lists).
+#define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
-cudaError_t launch_knn(const KnnParams& p, int emin, int emax, int grid, cudaStream_t s) {
-#define CCM_LAUNCH(A, B) \
-  if (emin == A && emax == B) return launch_range<A, B>(p, grid, s);
-  CCM_FOR_RANGES(CCM_LAUNCH)
+cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s) {
+#define CCM_LAUNCH(EV)                                                          \
+  if (E == EV) {                                                                \
+    knn_fused_kernel<EV><<<grid, kThreads, kSmemBytes, s>>>(p);                 \
+    return cudaGetLastError();                                                  \
+  }
+  CCM_FOR_E(CCM_LAUNCH)
 #undef CCM_LAUNCH
-  if (emin >= 1 && emax <= kMaxE) return launch_range<1, 10>(p, grid, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t knn_prepare() {
-#define CCM_PREP(A, B)                           \
-  {                                              \
-    const cudaError_t e = prepare_range<A, B>(); \
-    if (e != cudaSuccess) return e;              \
+#define CCM_PREP(EV)                                                            \
+  {                                                                             \
+    const cudaError_t e = cudaFuncSetAttribute(                                 \
+        knn_fused_kernel<EV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes); \
+    if (e != cudaSuccess) return e;                                             \
   }
-  CCM_FOR_RANGES(CCM_PREP)
+  CCM_FOR_E(CCM_PREP)
 #undef CCM_PREP
   return cudaSuccess;
 }
 
-cudaError_t knn_occupancy(int emin, int emax, int* ctas) {
-#define CCM_OCC(A, B) \
-  if (emin == A && emax == B) return occupancy_range<A, B>(ctas);
-  CCM_FOR_RANGES(CCM_OCC)
+cudaError_t knn_occupancy(int E, int* ctas) {
+#define CCM_OCC(EV)                                                             \
+  if (E == EV)                                                                  \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_fused_kernel<EV>, kThreads, \
+                                                         kSmemBytes);
+  CCM_FOR_E(CCM_OCC)
 #undef CCM_OCC
-  if (emin >= 1 && emax <= kMaxE) return occupancy_range<1, 10>(ctas);
   return cudaErrorInvalidValue;
 }
 

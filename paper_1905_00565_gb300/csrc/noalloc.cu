@@ -207,6 +207,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   SamplerParams sp{};
   sp.units = reinterpret_cast<const UnitDesc*>(scratch + lay.units);
   sp.targets = reinterpret_cast<const TargetDesc*>(scratch + lay.target);
+  sp.order = reinterpret_cast<const int32_t*>(scratch + lay.order);
   sp.lib = reinterpret_cast<int32_t*>(scratch + lay.lib);
   sp.err = reinterpret_cast<int32_t*>(scratch + lay.err);
   e = launch_sampler(sp, 0, r, (int)n_m, s);
@@ -229,7 +230,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
     kp.merge_at[q] = kDefaultMergeAt;
     kp.variant[q] = kDefaultVariant;
   }
-  e = launch_knn(kp, E, E, (int)kp.n_items, s);
+  e = launch_knn(kp, E, (int)kp.n_items, s);
   if (e != cudaSuccess) return noalloc_fail(CCM_ECUDA, cudaGetErrorString(e));
   if (!cuda_stream) {
     int32_t err = 0;

@@ -5,6 +5,7 @@
 // every query, a sorted insertion into a local top-(E+2) list) that writes
 // the predictions, and a one-CTA FP64 Pearson kernel.  Same selection rule and
 // rounding sequence as the fused kernel, hence the same neighbours.
+#include <limits.h>
 #include <math.h>
 
 #include "ccm_internal.h"
@@ -32,7 +33,7 @@ plain_knn_kernel(const float* series, const UnitDesc* unit, const TargetDesc* ta
   int kl[kMaxE + 2];
   for (int s = 0; s < K; ++s) {
     kd[s] = INFINITY;
-    kl[s] = -1;
+    kl[s] = INT_MAX;
   }
   for (int a = 0; a < u.L; ++a) {
     const int l = ul[a];
@@ -43,9 +44,10 @@ plain_knn_kernel(const float* series, const UnitDesc* unit, const TargetDesc* ta
       diff = __fsub_rn(q[e], sj[l + off - e * tau]);
       acc = __fmaf_rn(diff, diff, acc);
     }
-    if (acc < kd[K - 1]) {
+    // (distance, index) order: the library may be listed in any order
+    if (acc < kd[K - 1] || (acc == kd[K - 1] && l < kl[K - 1])) {
       int s = K - 1;
-      while (s > 0 && acc < kd[s - 1]) {
+      while (s > 0 && (acc < kd[s - 1] || (acc == kd[s - 1] && l < kl[s - 1]))) {
         kd[s] = kd[s - 1];
         kl[s] = kl[s - 1];
         --s;

@@ -133,8 +133,10 @@ bool all_finite(const float* x, size_t count) {
 struct UnitList {
   std::vector<UnitDesc> units;        // library realizations
   std::vector<TargetDesc> targets;    // their targets (one per output rho)
-  std::vector<WorkItem> items;
+  std::vector<WorkItem> items;        // brute-force items, grouped by E (see sort_items)
   std::vector<double> item_cost;
+  int64_t e_first[kMaxE + 1] = {};    // items of E: e_count[E] from index e_first[E]
+  int64_t e_count[kMaxE + 1] = {};
   std::vector<OrderJob> orders;       // one per (job, library variable, E, tau)
   std::vector<TableJob> tables;       // distance indexing tables to build
   std::vector<WorkItem> items_table;  // work items of units that read a table
@@ -345,7 +347,33 @@ void sort_by_cost(std::vector<WorkItem>* items, const std::vector<double>& cost)
 }
 
 void sort_items(UnitList* ul) {
-  sort_by_cost(&ul->items, ul->item_cost);
+  // Brute-force items: grouped by E (one single-E kernel launch per group,
+  // in the stream's order), larger items first within a group.
+  {
+    std::vector<int64_t> order(ul->items.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = (int64_t)q;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+      const int32_t ea = ul->units[(size_t)ul->items[(size_t)a].unit].E;
+      const int32_t eb = ul->units[(size_t)ul->items[(size_t)b].unit].E;
+      if (ea != eb) return ea > eb;
+      return ul->item_cost[(size_t)a] > ul->item_cost[(size_t)b];
+    });
+    std::vector<WorkItem> sorted(order.size());
+    std::vector<double> cost(order.size());
+    for (size_t q = 0; q < order.size(); ++q) {
+      sorted[q] = ul->items[(size_t)order[q]];
+      cost[q] = ul->item_cost[(size_t)order[q]];
+    }
+    ul->items.swap(sorted);
+    ul->item_cost.swap(cost);
+    for (int E = 0; E <= kMaxE; ++E) ul->e_first[E] = ul->e_count[E] = 0;
+    for (const WorkItem& w : ul->items) ++ul->e_count[ul->units[(size_t)w.unit].E];
+    int64_t at = 0;  // groups are stored from E = 10 down to E = 1
+    for (int E = kMaxE; E >= 1; --E) {
+      ul->e_first[E] = at;
+      at += ul->e_count[E];
+    }
+  }
   // Table items: grouped by table (a table of 20-80 MB stays in L2 while its
   // realizations run), larger items first within a table.
   std::vector<int64_t> order(ul->items_table.size());
@@ -384,7 +412,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.done = take(sizeof(uint32_t) * ul.units.size());
   a.rho = take(sizeof(double) * (size_t)n_rho);
   a.err = take(sizeof(int32_t));
-  a.counter = take(2 * sizeof(uint32_t));  // brute-force and table work counters
+  a.counter = take((kMaxE + 1) * sizeof(uint32_t));  // [0] table items, [E] brute force of E
   a.scratch = take(sizeof(float) * (size_t)scratch_floats);
   a.order = take(sizeof(int32_t) * (size_t)ul.order_total);
   a.orders = take(sizeof(OrderJob) * ul.orders.size());
@@ -524,6 +552,7 @@ SamplerParams sampler_params(char* base, const Arena& ar) {
   SamplerParams sp{};
   sp.units = reinterpret_cast<const UnitDesc*>(base + ar.units);
   sp.targets = reinterpret_cast<const TargetDesc*>(base + ar.targets);
+  sp.order = reinterpret_cast<const int32_t*>(base + ar.order);
   sp.lib = reinterpret_cast<int32_t*>(base + ar.lib);
   sp.err = reinterpret_cast<int32_t*>(base + ar.err);
   return sp;
@@ -569,7 +598,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                      : cudaEventRecord(e, s);
   };
   CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
-  CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, 2 * sizeof(uint32_t), s));
+  CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, (kMaxE + 1) * sizeof(uint32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
   if (ev) CCM_CUDA(record(ev[0]));
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
@@ -589,16 +618,24 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
   KnnParams kp = knn_params(base, ar, ul, persistent, tn);
   kp.dbg_nbr = dbg_nbr;
   kp.dbg_xhat = dbg_xhat;
-  if (!ul.items.empty()) {
-    const int g = persistent ? grid : (int)ul.items.size();
-    CCM_CUDA(launch_knn(kp, ul.emin, ul.emax, g, s));
+  // One launch per E (a kernel specialised for one E keeps its registers for
+  // that E); each drains its own queue, larger items first, so the launches
+  // follow each other with short tails.
+  for (int E = kMaxE; E >= 1; --E) {
+    if (ul.e_count[E] == 0) continue;
+    KnnParams ke = kp;
+    ke.items = kp.items + ul.e_first[E];
+    ke.n_items = ul.e_count[E];
+    ke.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter) + E;
+    const int g = persistent ? grid : (int)std::min<int64_t>(ul.e_count[E], 0x7fffffff);
+    CCM_CUDA(launch_knn(ke, E, g, s));
   }
   if (ev) CCM_CUDA(record(ev[3]));
   if (!ul.items_table.empty()) {
     KnnParams kt = kp;
     kt.items = reinterpret_cast<const WorkItem*>(base + ar.items_table);
     kt.n_items = (int64_t)ul.items_table.size();
-    kt.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter) + 1;
+    kt.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter);
     const int g = persistent ? grid_table : (int)ul.items_table.size();
     CCM_CUDA(launch_knn_table(kt, ul.max_nm, g, s));
   }
@@ -615,8 +652,13 @@ ccm_status check_err_flag(char* base, const Arena& ar, cudaStream_t s) {
 }
 
 int persistent_grid(ccm_context* ctx, int emin, int emax) {
-  int per_sm = 1;
-  if (knn_occupancy(emin, emax, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  int per_sm = 1 << 30;  // the smallest occupancy of the plan's kernels
+  for (int E = std::max(emin, 1); E <= std::min(emax, kMaxE); ++E) {
+    int c = 1;
+    if (knn_occupancy(E, &c) != cudaSuccess || c < 1) c = 1;
+    per_sm = std::min(per_sm, c);
+  }
+  if (per_sm == (1 << 30)) per_sm = 1;
   return ctx->sm_count * per_sm;
 }
 
@@ -705,7 +747,7 @@ ccm_status autotune(ccm_plan_s* pl, cudaStream_t s) {
     if (ce != cudaSuccess) { st = fail(CCM_ECUDA, cudaGetErrorString(ce)); break; }
     float best = 1e30f;
     int best_v = pl->tuning.variant[E], best_ma = pl->tuning.merge_at[E];
-    for (int v = 0; v <= (E <= 6 ? 1 : 0); ++v)
+    for (int v = 0; v < 2; ++v)
       for (int ma : {3, 6, 9}) {
         Tuning tn = pl->tuning;
         tn.variant[E] = v;
@@ -716,7 +758,7 @@ ccm_status autotune(ccm_plan_s* pl, cudaStream_t s) {
         float ms = 0.f;
         for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {  // warm-up, then timed
           ce = cudaEventRecord(e0, s);
-          if (ce == cudaSuccess) ce = launch_knn(kp, ul.emin, ul.emax, (int)sample.size(), s);
+          if (ce == cudaSuccess) ce = launch_knn(kp, E, (int)sample.size(), s);
           if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
           if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
           if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);

@@ -11,8 +11,10 @@
 // One CTA per unit.  The high halves h(m) are computed once into shared memory
 // (or recomputed per pass when N_m is too large), an 8-bit radix select over
 // four passes finds the L-th smallest key (h*, and how many of the h == h*
-// points, smallest m first, are taken), and an in-order block compaction
-// writes the chosen m ascending.
+// points, smallest m first, are taken).  An in-order block compaction over m
+// finds the largest tie taken (and writes the checking copy, ascending m); a
+// second one over the unit's query order writes the library in query order,
+// the order the neighbour search visits it in (spatially coherent runs).
 #include "ccm_internal.h"
 
 namespace ccm {
@@ -82,6 +84,7 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_prefix, s_rank;
+  __shared__ int s_mtie;
 
   const int64_t uidx = first_unit + blockIdx.x;
   const UnitDesc u = p.units[uidx];
@@ -96,6 +99,7 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
   if (threadIdx.x == 0) {
     s_prefix = 0u;
     s_rank = (uint32_t)L;  // 1-based rank still to find within the current prefix
+    s_mtie = -1;
   }
   uint32_t mask = 0u;
   for (int pass = 0; pass < 4; ++pass) {
@@ -143,22 +147,45 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
     if (threadIdx.x == 0) atomicOr(p.err, kErrSampler);
     return;
   }
-  int32_t* out = p.lib + u.lib_off;
   uint32_t w = out_before, tie_seen = tie_before;
   for (int m = m0; m < m1; ++m) {
     const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
     bool take = h < hstar;
     if (h == hstar) {
       take = tie_seen < take_ties;
+      if (take && tie_seen + 1 == take_ties) s_mtie = m;  // the last tie taken
       ++tie_seen;
     }
     if (take) {
-      out[w] = m;
       if (p.dbg_lib)  // checking copy, once per target of this library
         for (int t = 0; t < u.n_targets; ++t)
           p.dbg_lib[p.targets[u.tgt_off + t].lib_dbg_off + w] = m;
       ++w;
     }
+  }
+  __syncthreads();
+  const int mtie = s_mtie;  // members: h < h*, or h == h* and m <= mtie
+
+  // The library in query order: compaction over contiguous chunks of positions.
+  const int32_t* ord = p.order + u.order_off;
+  uint32_t n_mem = 0u;
+  for (int q = m0; q < m1; ++q) {
+    const int m = ord[q];
+    const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
+    n_mem += (h < hstar || (h == hstar && m <= mtie));
+  }
+  uint32_t pos_before;
+  const uint32_t total2 = block_exclusive_scan(n_mem, &pos_before, s_warp);
+  if (total2 != (uint32_t)L) {
+    if (threadIdx.x == 0) atomicOr(p.err, kErrSampler);
+    return;
+  }
+  int32_t* out = p.lib + u.lib_off;
+  w = pos_before;
+  for (int q = m0; q < m1; ++q) {
+    const int m = ord[q];
+    const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
+    if (h < hstar || (h == hstar && m <= mtie)) out[w++] = m;
   }
 }
 

@@ -159,6 +159,16 @@ def plain_ccm_problem(seed: int = DEFAULT_SEED + 1) -> Problem:
                    name="plain-ccm-n1000")
 
 
+def paper_scenario_problem(seed: int = DEFAULT_SEED + 6) -> Problem:
+    """The paper's baseline scenario (Sect. 4) on a synthetic stand-in: N=4000,
+    r=500, L in {500, 1000, 2000}, E and tau in {1, 2, 4}, both directions of the
+    coupled logistic map (the paper's series is unnamed and not available)."""
+    return Problem(series=logistic_pair(4000), pairs=BOTH_DIRECTIONS.copy(),
+                   E=np.array([1, 2, 4], np.int32), tau=np.array([1, 2, 4], np.int32),
+                   L=np.array([500, 1000, 2000], np.int64), r=500, seed=seed,
+                   name="paper-baseline-n4000")
+
+
 def sweep_problem(seed: int = DEFAULT_SEED + 2, n: int = 10_000, r: int = 250) -> Problem:
     """Batched sweep: N=10^4, E=1..10, tau=1..4, 20 L log-spaced 100..9000, r=250."""
     return Problem(series=logistic_pair(n), pairs=BOTH_DIRECTIONS.copy(),
