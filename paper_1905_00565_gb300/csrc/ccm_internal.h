@@ -55,9 +55,11 @@ struct OrderJob {
   int64_t series_off;   // element offset of the job's series block
   int64_t n;            // series length
   int64_t order_off;    // first entry of the order array of this combination
+  int64_t scratch_off;  // manifolds above kOrderMaxSort: 2*n_m 64-bit keys of scratch
+                        // from here (merge sort); -1: keep time order
   int32_t j, E, tau, n_m;
 };
-constexpr int kOrderMaxSort = 16384;   // manifolds up to this size are sorted
+constexpr int kOrderMaxSort = 16384;   // manifolds up to this size are sorted in one pass
 
 // Distance indexing table job: one per (job, library variable, E, tau) whose
 // realizations read their neighbours from a table.
@@ -123,7 +125,7 @@ cudaError_t launch_sampler(const SamplerParams& p, int64_t first_unit, int64_t c
 // Query order (order.cu).
 cudaError_t order_prepare();
 cudaError_t launch_order(const float* series, const OrderJob* jobs, int64_t n_jobs, int max_nm,
-                         int32_t* order, cudaStream_t s);
+                         int32_t* order, unsigned long long* scratch, cudaStream_t s);
 
 // Distance indexing table (table.cu).
 cudaError_t table_prepare();

@@ -126,6 +126,7 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     oj.series_off = 0;
     oj.n = c.n;
     oj.order_off = 0;
+    oj.scratch_off = -1;  // long manifolds keep time order here (no scratch)
     oj.j = c.j;
     oj.E = c.E;
     oj.tau = c.tau;
@@ -202,7 +203,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   c.n_tiles = (int32_t)n_tiles;
   noalloc_setup_kernel<<<(unsigned)((r * n_tiles + 255) / 256), 256, 0, s>>>(scratch, lay, c);
   e = launch_order(d_series, reinterpret_cast<const OrderJob*>(scratch + lay.orderjob), 1,
-                   (int)n_m, reinterpret_cast<int32_t*>(scratch + lay.order), s);
+                   (int)n_m, reinterpret_cast<int32_t*>(scratch + lay.order), nullptr, s);
   if (e != cudaSuccess) return noalloc_fail(CCM_ECUDA, cudaGetErrorString(e));
   SamplerParams sp{};
   sp.units = reinterpret_cast<const UnitDesc*>(scratch + lay.units);

@@ -10,7 +10,10 @@
 // 30/D bits over the series' [min, max]; ties (and the key's low half) by the
 // manifold index m, so the order is a deterministic function of the series.
 // One CTA per (variable, E, tau) sorts the 64-bit keys with a bitonic network
-// in shared memory when N_m <= kOrderMaxSort; longer manifolds keep time order.
+// in shared memory when N_m <= kOrderMaxSort; a longer manifold is sorted by
+// one CTA too: runs of kOrderMaxSort keys sorted in shared memory, then merged
+// pairwise in global scratch (merge path: every thread finds its output range
+// by a binary search on the diagonal), which gives the same order.
 #include <float.h>
 #include <stdint.h>
 
@@ -46,21 +49,11 @@ __device__ __forceinline__ uint32_t quantise(float c, float lo, float inv, int b
   return (uint32_t)v;
 }
 
-__global__ void __launch_bounds__(kOrderThreads)
-order_kernel(const float* series, const OrderJob* jobs, int32_t* order) {
-  extern __shared__ unsigned long long s_key[];
+// Series range of job jb (block-wide min/max).
+__device__ void series_range(const float* s, int64_t n, float* lo_out, float* hi_out) {
   __shared__ float s_lo[32], s_hi[32];
-  const OrderJob jb = jobs[blockIdx.x];
-  const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
-  const int n_m = jb.n_m, E = jb.E, tau = jb.tau, off = (E - 1) * tau;
-  int32_t* out = order + jb.order_off;
-  if (n_m > kOrderMaxSort) {  // long manifold: time order
-    for (int m = threadIdx.x; m < n_m; m += blockDim.x) out[m] = m;
-    return;
-  }
-  // series range
   float lo = FLT_MAX, hi = -FLT_MAX;
-  for (int64_t t = threadIdx.x; t < jb.n; t += blockDim.x) {
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
     lo = fminf(lo, s[t]);
     hi = fmaxf(hi, s[t]);
   }
@@ -79,47 +72,115 @@ order_kernel(const float* series, const OrderJob* jobs, int32_t* order) {
     lo = fminf(lo, s_lo[w]);
     hi = fmaxf(hi, s_hi[w]);
   }
-  const float inv = (hi > lo) ? 1.f / (hi - lo) : 0.f;
-  const int D = min(E, 3);
-  int n2 = 1;
-  while (n2 < n_m) n2 <<= 1;
-  for (int q = threadIdx.x; q < n2; q += blockDim.x) {
-    unsigned long long key = ~0ull;
-    if (q < n_m) {
-      const int t = q + off;
-      uint32_t code;
-      if (D == 1) {
-        code = quantise(s[t], lo, inv, 30);
-      } else if (D == 2) {
-        code = (spread2(quantise(s[t], lo, inv, 15)) << 1) | spread2(quantise(s[t - tau], lo, inv, 15));
-      } else {
-        code = (spread3(quantise(s[t], lo, inv, 10)) << 2) |
-               (spread3(quantise(s[t - tau], lo, inv, 10)) << 1) |
-               spread3(quantise(s[t - 2 * tau], lo, inv, 10));
-      }
-      key = ((unsigned long long)code << 32) | (unsigned)q;
-    }
-    s_key[q] = key;
-  }
   __syncthreads();
-  // bitonic sort, ascending
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+  *lo_out = lo;
+  *hi_out = hi;
+}
+
+// Sort key of manifold point q: (Morton code << 32) | q.
+__device__ __forceinline__ unsigned long long morton_key(const float* s, int off, int tau, int E,
+                                                         float lo, float inv, int q) {
+  const int t = q + off;
+  const int D = min(E, 3);
+  uint32_t code;
+  if (D == 1) {
+    code = quantise(s[t], lo, inv, 30);
+  } else if (D == 2) {
+    code = (spread2(quantise(s[t], lo, inv, 15)) << 1) | spread2(quantise(s[t - tau], lo, inv, 15));
+  } else {
+    code = (spread3(quantise(s[t], lo, inv, 10)) << 2) |
+           (spread3(quantise(s[t - tau], lo, inv, 10)) << 1) |
+           spread3(quantise(s[t - 2 * tau], lo, inv, 10));
+  }
+  return ((unsigned long long)code << 32) | (unsigned)q;
+}
+
+// Ascending bitonic sort of n2 (a power of two) keys in shared memory.
+__device__ void bitonic_sort(unsigned long long* k, int n2) {
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int jj = size >> 1; jj > 0; jj >>= 1) {
       for (int q = threadIdx.x; q < n2; q += blockDim.x) {
         const int p = q ^ jj;
         if (p > q) {
-          const unsigned long long a = s_key[q], b = s_key[p];
-          const bool up = (q & k) == 0;
+          const unsigned long long a = k[q], b = k[p];
+          const bool up = (q & size) == 0;
           if ((a > b) == up) {
-            s_key[q] = b;
-            s_key[p] = a;
+            k[q] = b;
+            k[p] = a;
           }
         }
       }
       __syncthreads();
     }
   }
-  for (int q = threadIdx.x; q < n_m; q += blockDim.x) out[q] = (int32_t)(s_key[q] & 0xffffffffu);
+}
+
+__global__ void __launch_bounds__(kOrderThreads)
+order_kernel(const float* series, const OrderJob* jobs, int32_t* order,
+             unsigned long long* scratch) {
+  extern __shared__ unsigned long long s_key[];
+  const OrderJob jb = jobs[blockIdx.x];
+  const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
+  const int n_m = jb.n_m, E = jb.E, tau = jb.tau, off = (E - 1) * tau;
+  int32_t* out = order + jb.order_off;
+  if (n_m > kOrderMaxSort && jb.scratch_off < 0) {  // no scratch: time order
+    for (int m = threadIdx.x; m < n_m; m += blockDim.x) out[m] = m;
+    return;
+  }
+  float lo, hi;
+  series_range(s, jb.n, &lo, &hi);
+  const float inv = (hi > lo) ? 1.f / (hi - lo) : 0.f;
+  if (n_m <= kOrderMaxSort) {
+    int n2 = 1;
+    while (n2 < n_m) n2 <<= 1;
+    for (int q = threadIdx.x; q < n2; q += blockDim.x)
+      s_key[q] = (q < n_m) ? morton_key(s, off, tau, E, lo, inv, q) : ~0ull;
+    __syncthreads();
+    bitonic_sort(s_key, n2);
+    for (int q = threadIdx.x; q < n_m; q += blockDim.x) out[q] = (int32_t)(s_key[q] & 0xffffffffu);
+    return;
+  }
+  // Long manifold: sorted runs of kOrderMaxSort keys, then pairwise merges.
+  unsigned long long* buf[2] = {scratch + jb.scratch_off, scratch + jb.scratch_off + n_m};
+  for (int r0 = 0; r0 < n_m; r0 += kOrderMaxSort) {
+    const int len = min(kOrderMaxSort, n_m - r0);
+    for (int q = threadIdx.x; q < kOrderMaxSort; q += blockDim.x)
+      s_key[q] = (q < len) ? morton_key(s, off, tau, E, lo, inv, r0 + q) : ~0ull;
+    __syncthreads();
+    bitonic_sort(s_key, kOrderMaxSort);
+    for (int q = threadIdx.x; q < len; q += blockDim.x) buf[0][r0 + q] = s_key[q];
+    __syncthreads();
+  }
+  int src = 0;
+  for (int width = kOrderMaxSort; width < n_m; width <<= 1, src ^= 1) {
+    const unsigned long long* in = buf[src];
+    unsigned long long* dst = buf[src ^ 1];
+    for (int b0 = 0; b0 < n_m; b0 += 2 * width) {
+      const int a_len = min(width, n_m - b0);
+      const int b_len = max(0, min(width, n_m - b0 - width));
+      const unsigned long long* A = in + b0;
+      const unsigned long long* B = in + b0 + a_len;
+      const int total = a_len + b_len;
+      const int per = (total + blockDim.x - 1) / blockDim.x;
+      const int k0 = min(total, (int)threadIdx.x * per), k1 = min(total, k0 + per);
+      if (k0 < k1) {
+        // merge path: i keys from A and k0 - i from B precede output k0 (keys are distinct)
+        int lo_i = max(0, k0 - b_len), hi_i = min(k0, a_len);
+        while (lo_i < hi_i) {
+          const int mid = (lo_i + hi_i) >> 1;
+          if (A[mid] < B[k0 - 1 - mid]) lo_i = mid + 1;
+          else hi_i = mid;
+        }
+        int i = lo_i, jv = k0 - lo_i;
+        for (int k = k0; k < k1; ++k) {
+          const bool take_a = jv >= b_len || (i < a_len && A[i] < B[jv]);
+          dst[b0 + k] = take_a ? A[i++] : B[jv++];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < n_m; q += blockDim.x) out[q] = (int32_t)(buf[src][q] & 0xffffffffu);
 }
 
 }  // namespace
@@ -130,12 +191,12 @@ cudaError_t order_prepare() {
 }
 
 cudaError_t launch_order(const float* series, const OrderJob* jobs, int64_t n_jobs, int max_nm,
-                         int32_t* order, cudaStream_t s) {
+                         int32_t* order, unsigned long long* scratch, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
   int n2 = 1;
   while (n2 < max_nm && n2 < kOrderMaxSort) n2 <<= 1;
   const size_t smem = (size_t)n2 * sizeof(unsigned long long);
-  order_kernel<<<(unsigned)n_jobs, kOrderThreads, smem, s>>>(series, jobs, order);
+  order_kernel<<<(unsigned)n_jobs, kOrderThreads, smem, s>>>(series, jobs, order, scratch);
   return cudaGetLastError();
 }
 

@@ -142,6 +142,7 @@ struct UnitList {
   std::vector<WorkItem> items_table;  // work items of units that read a table
   std::vector<double> item_cost_table;
   int64_t lib_total = 0, part_total = 0, order_total = 0, table_total = 0;
+  int64_t order_scratch_total = 0;    // 64-bit keys for sorting manifolds above kOrderMaxSort
   int max_R = 0;
   double brute_flops = 0.0;           // 3E per pair of the units searched by brute force
   int table_u16() const { return max_nm < 65536 ? 1 : 0; }
@@ -205,12 +206,17 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         oj.series_off = series_off;
         oj.n = pc.n;
         oj.order_off = ul->order_total;
+        oj.scratch_off = -1;
         oj.j = j;
         oj.E = E;
         oj.tau = tau;
         oj.n_m = (int32_t)(pc.n - (int64_t)(E - 1) * tau);
         combo[std::make_tuple(j, E, tau)] = oj.order_off;
         ul->order_total += oj.n_m;
+        if (oj.n_m > kOrderMaxSort) {
+          oj.scratch_off = ul->order_scratch_total;
+          ul->order_scratch_total += 2 * (int64_t)oj.n_m;
+        }
         ul->orders.push_back(oj);
       }
   // Distance indexing tables (CCM_TABLE): per (j, E, tau), realizations with
@@ -393,7 +399,7 @@ void sort_items(UnitList* ul) {
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
          counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
-         items_table = 0, total = 0;
+         items_table = 0, order_scratch = 0, total = 0;
 };
 
 Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
@@ -415,6 +421,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.counter = take((kMaxE + 1) * sizeof(uint32_t));  // [0] table items, [E] brute force of E
   a.scratch = take(sizeof(float) * (size_t)scratch_floats);
   a.order = take(sizeof(int32_t) * (size_t)ul.order_total);
+  a.order_scratch = take(sizeof(unsigned long long) * (size_t)ul.order_scratch_total);
   a.orders = take(sizeof(OrderJob) * ul.orders.size());
   a.targets = take(sizeof(TargetDesc) * ul.targets.size());
   a.table = take(ul.table_elem() * (size_t)ul.table_total);
@@ -604,7 +611,8 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
                         reinterpret_cast<const OrderJob*>(base + ar.orders),
                         (int64_t)ul.orders.size(), ul.max_nm,
-                        reinterpret_cast<int32_t*>(base + ar.order), s));
+                        reinterpret_cast<int32_t*>(base + ar.order),
+                        reinterpret_cast<unsigned long long*>(base + ar.order_scratch), s));
   CCM_CUDA(launch_table_build(reinterpret_cast<const float*>(base + ar.series),
                               reinterpret_cast<const TableJob*>(base + ar.tables),
                               (int64_t)ul.tables.size(), ul.max_nm, ul.max_R,
@@ -724,7 +732,8 @@ ccm_status autotune(ccm_plan_s* pl, cudaStream_t s) {
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
                         reinterpret_cast<const OrderJob*>(base + ar.orders),
                         (int64_t)ul.orders.size(), ul.max_nm,
-                        reinterpret_cast<int32_t*>(base + ar.order), s));
+                        reinterpret_cast<int32_t*>(base + ar.order),
+                        reinterpret_cast<unsigned long long*>(base + ar.order_scratch), s));
   SamplerParams sp = sampler_params(base, ar);
   CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
   const int want = 6 * ctx->sm_count;
@@ -1044,7 +1053,8 @@ ccm_status ccm_run_plain(ccm_plan_t* plan, const float* series, double* rho, voi
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
                         reinterpret_cast<const OrderJob*>(base + ar.orders),
                         (int64_t)plan->ul.orders.size(), plan->ul.max_nm,
-                        reinterpret_cast<int32_t*>(base + ar.order), s));
+                        reinterpret_cast<int32_t*>(base + ar.order),
+                        reinterpret_cast<unsigned long long*>(base + ar.order_scratch), s));
   for (size_t q = 0; q < plan->ul.units.size(); ++q) {
     const UnitDesc& u = plan->ul.units[q];
     CCM_CUDA(launch_sampler(sp, (int64_t)q, 1, u.n_m, s));
