@@ -203,8 +203,8 @@ def time_cpu_oracle(p, n_units: int):
 
 # ------------------------------------------------------------ GPU arm ------
 def traffic_entry():
-    """DRAM bytes per fused-kernel launch from the committed ncu summary, if the
-    kernel source still matches the one that was profiled."""
+    """DRAM bytes of the fused kernels per sweep (ten per-E launches) from the
+    committed ncu summary, if the kernel source still matches the profiled one."""
     try:
         rec = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
@@ -212,7 +212,7 @@ def traffic_entry():
     h = hashlib.sha256(open(KNN_SRC, "rb").read()).hexdigest()
     if rec.get("knn_fused_sha256") != h:
         return None
-    return rec.get("dram_bytes_per_full_sweep_launch")
+    return rec.get("dram_bytes_per_full_sweep")
 
 
 def run_ours(args, rank, world, local_rank):
@@ -312,7 +312,10 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic_entry(),
-                         "kernel": "knn_fused (3E FP32 flops per query-library pair)",
+                         "traffic_unit": "DRAM bytes per sweep (ten per-E launches)",
+                         "kernel": "knn_fused_kernel<E>, E=1..10, one launch per E per sweep "
+                                   "(3E FP32 flops per query-library pair, counting the pairs "
+                                   "that exact chunk pruning skips)",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "e2e": {"value": job_throughput(n_units, world, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": int(p.series.nbytes) + int(rho_host.nbytes),
