@@ -5,17 +5,20 @@ Workload (one "step"): the batched parameter sweep over a coupled logistic map
 of N=10^4 FP32 points: E=1..10, tau=1..4, 20 library sizes log-spaced 100..9000,
 r=250 realizations, both directions (800 cells x 250 x 2 = 4*10^5
 realizations, 4.0*10^9 neighbour queries, 8.45*10^12 query-library pairs).
-One step = one ccm_run of the whole sweep (query order, library sampler and
-one persistent fused kNN/simplex/rho launch, replayed from a CUDA graph)
-followed by ccm_convergence, the per-(pair, E, tau) convergence decision on
-the rho grid.
+One step = one ccm_run of the whole sweep with the library's defaults (query
+order, distance indexing tables for the large-L realizations, library
+sampler, one persistent brute-force fused kNN/simplex/rho launch per E for the
+rest, one table-scan launch; replayed from a CUDA graph) followed by
+ccm_convergence, the per-(pair, E, tau) convergence decision on the rho grid.
 
 Prints one JSON line.  `value` is realizations/s with inputs resident on the
 device; `e2e` is the same metric through ccm_run with pinned host buffers
 (host->device series copy and device->host rho copy inside the timed region);
-`roofline` reports the fused kernel against the FP32 ALU peak; `cpu_baseline`
-is the CPU oracle on a bounded sample of the same workload; `vs_plain_gpu`
-compares with the one-launch-per-realization plain GPU CCM on a subset.
+`roofline` reports the dominant kernel (the brute-force fused kernels) against
+the FP32 ALU peak; `brute_force_variant` is the same sweep without tables;
+`cpu_baseline` is the CPU oracle on a bounded sample of the same workload;
+`vs_plain_gpu` compares with the one-launch-per-realization plain GPU CCM on a
+subset.
 
 Multi-GPU (torchrun): every rank runs its own replica of the sweep (no data
 exchange); the barrier and a max-reduction of the timings are the only
@@ -58,7 +61,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-table", action="store_true")
+    ap.add_argument("--no-brute", action="store_true",
+                    help="skip the brute-force-only (CCM_NO_TABLE) variant")
     ap.add_argument("--serving-jobs", type=int, default=40)
     ap.add_argument("--scenario", default="", choices=["", "paper"],
                     help="paper: the paper's baseline scenario and its one-at-a-time "
@@ -210,7 +214,7 @@ def traffic_entry():
     except (OSError, ValueError):
         return None
     h = hashlib.sha256(open(KNN_SRC, "rb").read()).hexdigest()
-    if rec.get("knn_fused_sha256") != h:
+    if rec.get("knn_fused_sha256") != h or rec.get("path") != "default":
         return None
     return rec.get("dram_bytes_per_full_sweep")
 
@@ -247,7 +251,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, knn_ms, samp_ms, conv_ms = [], [], [], []
+    step_ms, stage_ms, conv_ms = [], [], []
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)
@@ -262,9 +266,7 @@ def run_ours(args, rank, world, local_rank):
         stream.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         conv_ms.append(em.elapsed_time(e1))
-        a, b = ccm.ccm_plan_kernel_times(plan)
-        samp_ms.append(a)
-        knn_ms.append(b)
+        stage_ms.append(ccm.ccm_plan_stage_times(plan))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -293,8 +295,9 @@ def run_ours(args, rank, world, local_rank):
     out = None
     if rank == 0:
         n_units = info["n_units"]
-        knn = sum(knn_ms) / len(knn_ms)
-        achieved = info["flop_count"] / (knn / 1e3) / 1e12
+        st = [sum(x[q] for x in stage_ms) / len(stage_ms) for q in range(4)]
+        # dominant kernel: the brute-force fused kernels (small-L realizations)
+        achieved = info["brute_flop_count"] / (st[2] / 1e3) / 1e12
         out = {
             "metric": METRIC, "value": job_throughput(n_units, world, t_step / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -304,32 +307,40 @@ def run_ours(args, rank, world, local_rank):
                            parallelism="replicas" if world > 1 else "single GPU"),
             "queries_per_s": info["n_queries"] * world / (t_step / 1e3),
             "pairs_per_s": info["pair_count"] * world / (t_step / 1e3),
-            "kernel_ms": {"sampler": sum(samp_ms) / len(samp_ms), "knn_fused": knn,
+            "kernel_ms": {"order_and_tables": st[0], "sampler": st[1],
+                          "knn_fused_brute_force": st[2], "knn_table_scan": st[3],
                           "convergence": sum(conv_ms) / len(conv_ms)},
+            "neighbour_search": {
+                "tables": "distance indexing tables (paper Sect. 3.2), built every step, for "
+                          "L >= sqrt(190 N_m/(E+1)); brute force with exact chunk pruning below",
+                "table_bytes": info["table_bytes"],
+                "brute_force_share_of_pairs": info["brute_flop_count"] / info["flop_count"]},
             "convergence": {"rows": n_rows, "converged_rows": int(conv_host["converged"].sum()),
                             "test": "one-sided Jonckheere-Terpstra over the 20 L groups, "
                                     "z > 1.645"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic_entry(),
-                         "traffic_unit": "DRAM bytes per sweep (ten per-E launches)",
-                         "kernel": "knn_fused_kernel<E>, E=1..10, one launch per E per sweep "
-                                   "(3E FP32 flops per query-library pair, counting the pairs "
-                                   "that exact chunk pruning skips)",
+                         "traffic_unit": "DRAM bytes per step, all brute-force launches",
+                         "kernel": "knn_fused_kernel<E> (brute force), one launch per E per step "
+                                   "over the realizations below the table threshold; 3E FP32 "
+                                   "flops per query-library pair, counting the pairs that exact "
+                                   "chunk pruning skips",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "e2e": {"value": job_throughput(n_units, world, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": int(p.series.nbytes) + int(rho_host.nbytes),
                     "d2h_bytes_per_step": int(rho_host.nbytes) + int(conv_host.nbytes),
                     "ms_per_step": e2e_t * 1e3, "same_rho_as_device_path": same},
-            # per step: query order, sampler, fused kNN, convergence
-            "gpu_launches": 4 * args.steps,
+            # per step: query order, tables, sampler, brute force per E, table scan,
+            # convergence
+            "gpu_launches": (info["launches_per_run"] + 1) * args.steps,
             "clocks": clk,
             "rho_finite": rho_ok,
         }
-        if not args.no_table:
-            tv = table_variant(ccm, ctx, p, torch, args.steps, 1, rho_dev, flush, stream)
-            tv["speedup_vs_brute_force"] = tv["value"] / out["value"]
-            out["table_variant"] = tv
+        if not args.no_brute:
+            bv = brute_variant(ccm, ctx, p, torch, args.steps, 1, rho_dev, flush, stream)
+            bv["default_speedup"] = out["value"] / bv["value"]
+            out["brute_force_variant"] = bv
         if not args.no_plain:
             out["vs_plain_gpu"] = compare_plain(ccm, ctx, I, p, torch)
         if not args.no_serving:
@@ -391,11 +402,10 @@ def serve_stream(ccm, I, n_jobs: int, device: int):
             "makespan_s": span2}
 
 
-def table_variant(ccm, ctx, p, torch, steps: int, warmup: int, rho_ref, flush, stream):
-    """The same sweep with distance indexing tables (paper Sect. 3.2): large-L
-    realizations read their neighbours from per-(variable, E, tau) tables of
-    each point's nearest points; results are bit-identical to brute force."""
-    flags = ccm.CCM_INPUT_ON_DEVICE | ccm.CCM_OUTPUT_ON_DEVICE | ccm.CCM_TABLE
+def brute_variant(ccm, ctx, p, torch, steps: int, warmup: int, rho_ref, flush, stream):
+    """The same sweep with CCM_NO_TABLE: every realization searched by the
+    brute-force fused kernels (with exact chunk pruning); bit-identical rho."""
+    flags = ccm.CCM_INPUT_ON_DEVICE | ccm.CCM_OUTPUT_ON_DEVICE | ccm.CCM_NO_TABLE
     plan = ccm.plan_problem(ctx, p, flags)
     info = ccm.ccm_plan_get_info(plan)
     s_dev = torch.from_numpy(p.series).cuda()
@@ -419,12 +429,11 @@ def table_variant(ccm, ctx, p, torch, steps: int, warmup: int, rho_ref, flush, s
     ccm.ccm_plan_destroy(plan)
     t = sum(step_ms) / len(step_ms)
     st = [sum(x[q] for x in stages) / len(stages) for q in range(4)]
+    achieved = info["flop_count"] / (st[2] / 1e3) / 1e12
     return {"value": info["n_units"] / (t / 1e3), "unit": UNIT, "ms_per_step": t,
-            "stage_ms": {"order_and_tables": st[0], "sampler": st[1], "brute_force_knn": st[2],
-                         "table_scan_knn": st[3]},
-            "table_bytes": info["table_bytes"],
-            "brute_force_share_of_flops": info["brute_flop_count"] / info["flop_count"],
-            "same_rho_bits_as_brute_force": same}
+            "stage_ms": {"order": st[0], "sampler": st[1], "knn_fused_brute_force": st[2]},
+            "roofline_frac": achieved / FP32_PEAK_TFLOPS, "achieved_tflops": achieved,
+            "same_rho_bits_as_default": same}
 
 
 def compare_plain(ccm, ctx, I, p, torch):
@@ -501,7 +510,7 @@ def paper_scenario(args):
     res = {}
     for name, p in cases.items():
         row = {"realizations": p.n_units()}
-        for label, flags in (("gpu_ms", dev), ("gpu_table_ms", dev | ccm.CCM_TABLE)):
+        for label, flags in (("gpu_ms", dev | ccm.CCM_NO_TABLE), ("gpu_table_ms", dev)):
             plan = ccm.plan_problem(ctx, p, flags)
             rho = torch.zeros(ccm.rho_shape(p), dtype=torch.float64, device="cuda")
             for _ in range(max(3, args.warmup)):

@@ -66,8 +66,12 @@ typedef enum {
 #define CCM_INPUT_ON_DEVICE  0x1u  /* series pointers given to ccm_run are device memory */
 #define CCM_OUTPUT_ON_DEVICE 0x2u  /* rho (and debug outputs) given to ccm_run are device memory */
 #define CCM_NO_AUTOTUNE      0x4u  /* keep cached or default kernel parameters (see ccm_run) */
-#define CCM_TABLE            0x8u  /* large-L realizations read neighbours from distance
-                                      indexing tables (paper Sect. 3.2); same results */
+#define CCM_NO_TABLE         0x10u /* brute-force search for every realization: no distance
+                                      indexing tables (paper Sect. 3.2).  By default,
+                                      realizations with large L read their neighbours from
+                                      per-(variable, E, tau) tables built in the same run,
+                                      where that is faster and the tables fit a quarter of
+                                      the context budget; results are identical either way */
 
 typedef struct {
   int32_t n_series;        /* V >= 2 series, each of length n */
@@ -82,7 +86,8 @@ typedef struct {
   const int64_t* L;        /* [n_L], each E+2 <= L <= N_m for every (E, tau) of the grid */
   int32_t r;               /* realizations per (pair, E, tau, L) cell, >= 1 */
   uint64_t seed;           /* library sampler seed */
-  uint32_t flags;          /* CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE | ... */
+  uint32_t flags;          /* CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE | CCM_NO_AUTOTUNE |
+                              CCM_NO_TABLE; other bits are refused (CCM_EINVAL) */
   /* Two options the paper does not discuss (common CCM variants); zero for the
    * paper's method.  theiler: exclusion window W >= 0, library point l is a
    * neighbour candidate of query m only when |l - m| > W (W = 0 excludes m
@@ -114,7 +119,8 @@ typedef struct {
   double pair_count;          /* query-library pairs = sum over units of N_m*L */
   double flop_count;          /* 3E FP32 flops per pair, summed */
   double brute_flop_count;    /* the part of flop_count searched by brute force */
-  size_t table_bytes;         /* distance indexing tables (CCM_TABLE), 0 without */
+  size_t table_bytes;         /* distance indexing tables of the plan (0: none) */
+  int64_t launches_per_run;   /* kernel launches of one ccm_run (graph nodes) */
 } ccm_plan_info;
 
 typedef struct ccm_context ccm_context;
@@ -137,8 +143,11 @@ ccm_status ccm_plan_destroy(ccm_plan_t* plan);
 
 ccm_status ccm_plan_get_info(const ccm_plan_t* plan, ccm_plan_info* info);
 
-/* Run the whole sweep: sampler, fused kNN + simplex + rho kernel (one
- * persistent launch), replayed from a CUDA graph after the first call.
+/* Run the whole sweep: query order, distance indexing tables (unless
+ * CCM_NO_TABLE or none pays off), library sampler, one persistent fused
+ * kNN + simplex + rho kernel per E for the brute-force realizations and one
+ * table-scan kernel for the rest; replayed from a CUDA graph after the first
+ * call.
  * series: [n_series][n] FP32 (host unless CCM_INPUT_ON_DEVICE); rho: FP64 as
  * above (host unless CCM_OUTPUT_ON_DEVICE).  cuda_stream: a cudaStream_t, or
  * NULL to run on the plan's own stream and block until done.  With a caller

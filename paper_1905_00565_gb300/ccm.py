@@ -34,7 +34,7 @@ CCM_ENOTFOUND = -7
 CCM_INPUT_ON_DEVICE = 0x1
 CCM_OUTPUT_ON_DEVICE = 0x2
 CCM_NO_AUTOTUNE = 0x4
-CCM_TABLE = 0x8
+CCM_NO_TABLE = 0x10
 
 STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM",
                 -3: "CCM_ETOOLARGE", -4: "CCM_ECUDA", -5: "CCM_ETIMEOUT",
@@ -68,7 +68,8 @@ class ccm_plan_info(ctypes.Structure):
                 ("library_entries", ctypes.c_int64), ("neighbour_entries", ctypes.c_int64),
                 ("n_work_items", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("pair_count", ctypes.c_double), ("flop_count", ctypes.c_double),
-                ("brute_flop_count", ctypes.c_double), ("table_bytes", ctypes.c_size_t)]
+                ("brute_flop_count", ctypes.c_double), ("table_bytes", ctypes.c_size_t),
+                ("launches_per_run", ctypes.c_int64)]
 
 
 class CCMError(RuntimeError):

@@ -73,6 +73,7 @@ struct TableJob {
 };
 constexpr int kTableMaxR = 2048;       // entries per query row, at most
 constexpr int kTableChunk = 8;         // query tiles per table work item (one bitmap each)
+constexpr int kTableMaxNm = 1 << 20;   // longest manifold that gets a table (bitmap in smem)
 
 // Sampler: one CTA per unit.
 struct SamplerParams {
@@ -142,7 +143,7 @@ cudaError_t knn_occupancy(int E, int* ctas_per_sm);
 cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s);
 // Table path: same work items, neighbours read from the distance indexing table.
 size_t knn_table_smem(int max_nm);
-cudaError_t knn_table_prepare(int max_nm);
+cudaError_t knn_table_prepare();
 cudaError_t knn_table_occupancy(int max_nm, int* ctas_per_sm);
 cudaError_t launch_knn_table(const KnnParams& p, int max_nm, int grid, cudaStream_t s);
 

@@ -696,9 +696,11 @@ size_t knn_table_smem(int max_nm) {
   return (size_t)kStageBytes + kHitBytes + (size_t)((max_nm + 31) / 32) * 4 + 16;
 }
 
-cudaError_t knn_table_prepare(int max_nm) {
+cudaError_t knn_table_prepare() {
+  // the largest bitmap any plan may need (manifolds up to kTableMaxNm points);
+  // set once, so that plans of different sizes never lower it for each other
   return cudaFuncSetAttribute(knn_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)knn_table_smem(max_nm));
+                              (int)knn_table_smem(kTableMaxNm));
 }
 
 cudaError_t knn_table_occupancy(int max_nm, int* ctas) {

@@ -93,6 +93,9 @@ ccm_status copy_problem(const ccm_problem* p, ProblemCopy* pc) {
   pc->r = p->r;
   pc->seed = p->seed;
   pc->flags = p->flags;
+  if (p->flags & ~(uint32_t)(CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE | CCM_NO_AUTOTUNE |
+                             CCM_NO_TABLE))
+    return fail(CCM_EINVAL, "unknown flag bits");
   pc->theiler = p->theiler;
   pc->weight_floor = p->weight_floor;
   if (p->theiler < 0) return fail(CCM_EINVAL, "theiler window must be >= 0");
@@ -153,19 +156,21 @@ struct UnitList {
 };
 
 // Smallest L whose realizations read a distance indexing table.  A table
-// scan visits about (E+1)*N_m/L rows per query, brute force about L library
-// points; measured on GB300 (N_m = 10^4, E = 1..10) the two cost the same at
-// L = 520..800, i.e. L ~ sqrt(48*N_m).  Below that brute force is faster.
-// The last term keeps R = 4(E+2)N_m/L + 64 within kTableMaxR.
+// scan visits about (E+1)*N_m/L rows per query; brute force (with chunk
+// pruning) costs about L distance evaluations of E coordinates per query.
+// Measured on GB300 (N_m = 10^4) the two break even near L = 900 for E = 1
+// and L = 450 for E = 10, i.e. L ~ sqrt(190*N_m/(E+1)); below that brute
+// force is faster.  The last term keeps R = 4(E+2)N_m/L + 64 within kTableMaxR.
 double table_min_L(int32_t E, int64_t n_m) {
-  return std::max({256.0, std::ceil(std::sqrt(48.0 * (double)n_m)),
+  return std::max({256.0, std::ceil(std::sqrt(190.0 * (double)n_m / (double)(E + 1))),
                    std::ceil(4.0 * (E + 2) * (double)n_m / (double)(kTableMaxR - 64))});
 }
 
 // Append the units of one problem.  Offsets: series block, first rho index.
 // Pairs that share a library variable j share one library and one neighbour
 // search per (E, tau, L, k); each pair becomes a target of that unit.
-void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, UnitList* ul) {
+void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, UnitList* ul,
+                  double table_cap_bytes) {
   const int tileq = knn_block_threads() * knn_queries_per_thread();
   const int64_t nP = (int64_t)pc.pairs.size() / 2;
   const int64_t nE = (int64_t)pc.E.size(), nT = (int64_t)pc.tau.size(), nL = (int64_t)pc.L.size();
@@ -219,23 +224,27 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         }
         ul->orders.push_back(oj);
       }
-  // Distance indexing tables (CCM_TABLE): per (j, E, tau), realizations with
-  // L >= table_min_L read their neighbours from a table of the R nearest
-  // points of every query; R covers about four times the expected scan length
-  // (E+2)*N_m/L at the smallest such L (CCM_TABLE_SAFETY changes the four).
-  // A table is built only when the
+  // Distance indexing tables (unless CCM_NO_TABLE): per (j, E, tau),
+  // realizations with L >= table_min_L read their neighbours from a table of
+  // the R nearest points of every query; R covers about four times the
+  // expected scan length (E+2)*N_m/L at the smallest such L
+  // (CCM_TABLE_SAFETY changes the four).  A table is built only when the
   // realizations that use it would otherwise scan at least 8*N_m library
-  // points in total (its build costs about N_m^2 distance evaluations).
+  // points in total (its build costs about N_m^2 distance evaluations), and
+  // while the plan's tables stay within table_cap_bytes; the realizations of
+  // a (j, E, tau) without a table use brute force.
   std::map<std::tuple<int32_t, int32_t, int32_t>, std::pair<int64_t, int32_t>> table_of;
   // Safety factor of R over the expected scan length; CCM_TABLE_SAFETY trades
   // table memory for how often a query falls back to scanning its library.
   double safety = 4.0;
   if (const char* env = getenv("CCM_TABLE_SAFETY")) safety = std::max(0.01, atof(env));
-  if (pc.flags & CCM_TABLE) {
+  double table_bytes = 0.0;
+  if (!(pc.flags & CCM_NO_TABLE)) {
     for (int32_t j : lib_vars)
       for (int32_t E : pc.E)
         for (int32_t tau : pc.tau) {
           const int64_t n_m = pc.n - (int64_t)(E - 1) * tau;
+          if (n_m > kTableMaxNm) continue;
           const double ls = table_min_L(E, n_m);
           int64_t lmin = -1;
           double lsum = 0.0;
@@ -249,6 +258,9 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
           int64_t R = (int64_t)std::ceil(safety * (E + 2) * (double)n_m / (double)lmin) + 64 +
                       2 * (int64_t)pc.theiler;
           R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR), n_m);
+          const double bytes = (double)n_m * (double)R * (n_m < 65536 ? 2.0 : 4.0);
+          if (table_bytes + bytes > table_cap_bytes) continue;
+          table_bytes += bytes;
           TableJob tj;
           std::memset(&tj, 0, sizeof(tj));
           tj.series_off = series_off;
@@ -487,6 +499,12 @@ struct ccm_context {
   std::multimap<size_t, void*> pool_free;
   std::vector<void*> pool_all;
 };
+
+namespace {
+// Device memory the distance indexing tables of one plan (or served batch)
+// may take: a quarter of the context's budget.
+double table_cap(const ccm_context* ctx) { return 0.25 * (double)ctx->budget; }
+}  // namespace
 
 namespace {
 
@@ -822,6 +840,7 @@ ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context**
   CCM_CUDA(order_prepare());
   CCM_CUDA(table_prepare());
   CCM_CUDA(convergence_prepare());
+  CCM_CUDA(knn_table_prepare());
   size_t free_b = 0, total_b = 0;
   CCM_CUDA(cudaMemGetInfo(&free_b, &total_b));
   std::unique_ptr<ccm_context> ctx(new ccm_context());
@@ -841,7 +860,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   pl->ctx = ctx;
   ccm_status st = copy_problem(prob, &pl->pc);
   if (st != CCM_OK) return st;
-  append_units(pl->pc, 0, 0, &pl->ul);
+  append_units(pl->pc, 0, 0, &pl->ul, table_cap(ctx));
   sort_items(&pl->ul);
   const int64_t series_elems = (int64_t)pl->pc.V * pl->pc.n;
   pl->ar = layout(series_elems, pl->ul, pl->ul.n_rho, pl->ul.max_nm);
@@ -873,7 +892,6 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_arena + pl->ar.items_table, pl->ul.items_table.data(),
                    sizeof(WorkItem) * pl->ul.items_table.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !pl->ul.items_table.empty()) e = knn_table_prepare(pl->ul.max_nm);
   if (e == cudaSuccess)
     e = cudaMemset(pl->d_arena + pl->ar.done, 0, sizeof(uint32_t) * pl->ul.units.size());
   if (e != cudaSuccess) {
@@ -903,6 +921,11 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.flop_count = pl->ul.flops;
   in.brute_flop_count = pl->ul.brute_flops;
   in.table_bytes = pl->ul.table_elem() * (size_t)pl->ul.table_total;
+  // launches of one ccm_run: order, tables, sampler, one brute-force kernel
+  // per E present, the table scan
+  in.launches_per_run = 2 + (pl->ul.tables.empty() ? 0 : 1) +
+                        (pl->ul.items_table.empty() ? 0 : 1);
+  for (int E = 1; E <= kMaxE; ++E) in.launches_per_run += (pl->ul.e_count[E] > 0) ? 1 : 0;
   *out = pl.release();
   return CCM_OK;
 }
@@ -1153,9 +1176,9 @@ struct Batch {
 
 namespace {
 
-size_t job_footprint(const ProblemCopy& pc, double* pairs) {
+size_t job_footprint(const ccm_context* ctx, const ProblemCopy& pc, double* pairs) {
   UnitList ul;
-  append_units(pc, 0, 0, &ul);
+  append_units(pc, 0, 0, &ul, table_cap(ctx));
   *pairs = ul.pairs;
   return layout((int64_t)pc.V * pc.n, ul, ul.n_rho, 0).total;
 }
@@ -1174,7 +1197,7 @@ void CUDART_CB on_batch_done(void* arg) {
 ccm_status launch_batch(ccm_context* ctx, Batch* b) {
   int64_t series_elems = 0, out = 0;
   for (auto& j : b->jobs) {
-    append_units(j->pc, series_elems, out, &b->ul);
+    append_units(j->pc, series_elems, out, &b->ul, table_cap(ctx));
     series_elems += (int64_t)j->pc.V * j->pc.n;
     out += j->n_units;
   }
@@ -1191,24 +1214,28 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
   }
   // Descriptors go through pinned staging: a copy from pageable memory would
   // wait for earlier work on this (reused) stream.
-  const size_t ub = sizeof(UnitDesc) * b->ul.units.size();
-  const size_t ib = sizeof(WorkItem) * b->ul.items.size();
-  const size_t ob = sizeof(OrderJob) * b->ul.orders.size();
-  const size_t tb = sizeof(TargetDesc) * b->ul.targets.size();
-  b->meta_bytes = ub + ib + ob + tb;
+  // (units, work items, order jobs, targets, table jobs, table work items)
+  const void* src[6] = {b->ul.units.data(), b->ul.items.data(), b->ul.orders.data(),
+                        b->ul.targets.data(), b->ul.tables.data(), b->ul.items_table.data()};
+  const size_t len[6] = {sizeof(UnitDesc) * b->ul.units.size(),
+                         sizeof(WorkItem) * b->ul.items.size(),
+                         sizeof(OrderJob) * b->ul.orders.size(),
+                         sizeof(TargetDesc) * b->ul.targets.size(),
+                         sizeof(TableJob) * b->ul.tables.size(),
+                         sizeof(WorkItem) * b->ul.items_table.size()};
+  const size_t dst[6] = {b->ar.units, b->ar.items, b->ar.orders, b->ar.targets, b->ar.tables,
+                         b->ar.items_table};
+  b->meta_bytes = 0;
+  for (int q = 0; q < 6; ++q) b->meta_bytes += len[q];
   b->h_meta = pinned_get(ctx, b->meta_bytes);
   if (!b->h_meta) return fail(CCM_ENOMEM, "pinned allocation failed");
   char* hm = static_cast<char*>(b->h_meta);
-  std::memcpy(hm, b->ul.units.data(), ub);
-  std::memcpy(hm + ub, b->ul.items.data(), ib);
-  std::memcpy(hm + ub + ib, b->ul.orders.data(), ob);
-  std::memcpy(hm + ub + ib + ob, b->ul.targets.data(), tb);
-  CCM_CUDA(cudaMemcpyAsync(base + b->ar.units, hm, ub, cudaMemcpyHostToDevice, b->stream));
-  CCM_CUDA(cudaMemcpyAsync(base + b->ar.items, hm + ub, ib, cudaMemcpyHostToDevice, b->stream));
-  CCM_CUDA(cudaMemcpyAsync(base + b->ar.orders, hm + ub + ib, ob, cudaMemcpyHostToDevice,
-                           b->stream));
-  CCM_CUDA(cudaMemcpyAsync(base + b->ar.targets, hm + ub + ib + ob, tb, cudaMemcpyHostToDevice,
-                           b->stream));
+  for (int q = 0; q < 6; ++q) {
+    if (len[q] == 0) continue;
+    std::memcpy(hm, src[q], len[q]);
+    CCM_CUDA(cudaMemcpyAsync(base + dst[q], hm, len[q], cudaMemcpyHostToDevice, b->stream));
+    hm += len[q];
+  }
   CCM_CUDA(cudaMemsetAsync(base + b->ar.done, 0, sizeof(uint32_t) * b->ul.units.size(), b->stream));
   Tuning tn;
   {
@@ -1382,7 +1409,7 @@ ccm_status ccm_submit(ccm_context* ctx, const ccm_problem* prob, const float* se
   const size_t elems = (size_t)j->pc.V * (size_t)j->pc.n;
   if (!all_finite(series, elems)) return fail(CCM_EINVAL, "series holds a non-finite value");
   j->n_units = j->pc.n_units();
-  j->footprint = job_footprint(j->pc, &j->pairs);
+  j->footprint = job_footprint(ctx, j->pc, &j->pairs);
   if (j->footprint > ctx->budget)
     return fail(CCM_ETOOLARGE, "job footprint " + std::to_string(j->footprint) +
                                    " B exceeds the context budget");

@@ -83,13 +83,13 @@ def test_window_with_tables_equals_brute_force(ccm):
                   seed=base.seed, name="window-table", theiler=12, weight_floor=1e-4)
     ctx = ccm.ccm_context_create(0)
     try:
-        plan = ccm.plan_problem(ctx, p, ccm.CCM_TABLE)
+        plan = ccm.plan_problem(ctx, p)
         try:
             assert ccm.ccm_plan_get_info(plan)["table_bytes"] > 0
         finally:
             ccm.ccm_plan_destroy(plan)
-        r0, l0, n0, x0 = run_detailed(ccm, ctx, p, 0)
-        r1, l1, n1, x1 = run_detailed(ccm, ctx, p, ccm.CCM_TABLE)
+        r0, l0, n0, x0 = run_detailed(ccm, ctx, p, ccm.CCM_NO_TABLE)
+        r1, l1, n1, x1 = run_detailed(ccm, ctx, p, 0)
     finally:
         ccm.ccm_context_destroy(ctx)
     assert np.array_equal(n0, n1) and np.array_equal(x0, x1) and np.array_equal(r0, r1)

@@ -1,4 +1,4 @@
-"""Distance indexing tables (CCM_TABLE, paper Sect. 3.2) on the GPU.
+"""Distance indexing tables (paper Sect. 3.2; on by default) on the GPU.
 
 A realization that reads its neighbours from the table must give exactly what
 the brute-force search gives (same neighbour lists, same bits of rho): the
@@ -29,13 +29,14 @@ def ccm():
 
 
 def both_paths(ccm, ctx, p):
-    a = run_detailed(ccm, ctx, p, 0)
-    b = run_detailed(ccm, ctx, p, ccm.CCM_TABLE)
+    """(brute force everywhere, default with tables)"""
+    a = run_detailed(ccm, ctx, p, ccm.CCM_NO_TABLE)
+    b = run_detailed(ccm, ctx, p, 0)
     return a, b
 
 
 def uses_table(ccm, ctx, p):
-    plan = ccm.plan_problem(ctx, p, ccm.CCM_TABLE)
+    plan = ccm.plan_problem(ctx, p)
     try:
         return ccm.ccm_plan_get_info(plan)["table_bytes"] > 0
     finally:
@@ -97,14 +98,14 @@ def test_table_fallback_path(ccm, monkeypatch):
 
 def test_table_fallback_small_e_regression(ccm, monkeypatch):
     """E = 2, tau = 3 on the full 10^4-point series with short table rows: at
-    L = 700 some queries meet fewer than E+1 library members among their
+    L = 850 some queries meet fewer than E+1 library members among their
     table entries and scan their library; the scan must keep the whole sorted
     (distance, index) list."""
     monkeypatch.setenv("CCM_TABLE_SAFETY", "0.05")
     base = I.sweep_problem()
     p = I.Problem(series=base.series, pairs=np.array([[1, 0]], np.int32),
                   E=np.array([2], np.int32), tau=np.array([3], np.int32),
-                  L=np.array([700, 9000], np.int64), r=29, seed=base.seed, name="fallback-e2")
+                  L=np.array([850, 9000], np.int64), r=29, seed=base.seed, name="fallback-e2")
     ctx = ccm.ccm_context_create(0)
     try:
         assert uses_table(ccm, ctx, p)
@@ -123,8 +124,8 @@ def test_table_on_the_long_series_sampled(ccm):
     ctx = ccm.ccm_context_create(0)
     try:
         assert uses_table(ccm, ctx, p)
-        rho, lib, nbr, xh = run_detailed(ccm, ctx, p, ccm.CCM_TABLE)
-        rb, *_ = run_detailed(ccm, ctx, p, 0)
+        rho, lib, nbr, xh = run_detailed(ccm, ctx, p, 0)
+        rb, *_ = run_detailed(ccm, ctx, p, ccm.CCM_NO_TABLE)
     finally:
         ccm.ccm_context_destroy(ctx)
     np.testing.assert_array_equal(rho, rb)
