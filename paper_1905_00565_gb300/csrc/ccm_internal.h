@@ -145,7 +145,7 @@ cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s);
 size_t knn_table_smem(int max_nm);
 cudaError_t knn_table_prepare();
 cudaError_t knn_table_occupancy(int max_nm, int* ctas_per_sm);
-cudaError_t launch_knn_table(const KnnParams& p, int max_nm, int grid, cudaStream_t s);
+cudaError_t launch_knn_table(const KnnParams& p, int E, int max_nm, int grid, cudaStream_t s);
 
 // Sets the thread-local message returned by ccm_last_error() (runtime.cu).
 void set_last_error(const char* msg);

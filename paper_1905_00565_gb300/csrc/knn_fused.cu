@@ -257,16 +257,48 @@ __device__ __forceinline__ double merge_moments(const double* base, int n_tiles)
   return (SXX > 0.0 && SYY > 0.0) ? __ddiv_rn(SXY, __dsqrt_rn(__dmul_rn(SXX, SYY))) : nan("");
 }
 
+// Called by a tile's reducer warp after its lane 0 wrote every target's
+// moments of the tile: the fence orders them before the completion count, and
+// the last tile of the realization to arrive merges them all.  Out of line:
+// it runs once per tile, and inlined its registers would crowd the search.
+__device__ __noinline__ void complete_tile(const KnnParams& p, const UnitDesc& u, int unit) {
+  const int lane = threadIdx.x & 31;
+  unsigned prev = 0u;
+  if (lane == 0) {
+    __threadfence();
+    prev = atomicAdd(&p.unit_done[unit], 1u);
+  }
+  prev = __shfl_sync(kFull, prev, 0);
+  if (prev != (unsigned)(u.n_tiles - 1)) return;
+  __threadfence();
+  for (int t = 0; t < u.n_targets; ++t) {
+    const double r = merge_moments(p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles),
+                                   u.n_tiles);
+    if (lane == 0) p.rho[p.targets[u.tgt_off + t].out_idx] = r;
+  }
+  if (lane == 0) p.unit_done[unit] = 0u;  // ready for the next run
+}
+
 // Everything after the neighbour search, shared by the brute-force and the
 // table paths: dd[0..E] ascending FP32 squared distances and nb[0..E] the
 // neighbours of query m (itself excluded).  Simplex weights, the prediction
 // of every target, FP64 tile moments, and the merge of the moments by the
-// realization's last tile.  `stage` is 4*kQT doubles of shared memory that no
-// thread reads any more once every thread has arrived here.
-template <int E>
+// realization's last tile.
+//
+// `stage` is 4*kQT doubles of shared memory: two buffers, used alternately by
+// successive stagings; k0 numbers this tile's first staging within the work
+// item (the same in every thread; a work item starts behind block barriers).
+// One warp per tile (rotating with the tile index) reduces the tile's moments,
+// signals completion and, for the realization's last tile, merges; the other
+// warps go on.  Staging k writes its buffer after the barrier of staging k-1,
+// which the reducer of staging k-2 reaches only after it has finished with
+// that buffer.  kBarriers (brute-force path): the stage buffers overlap memory
+// the search still reads, so every thread arrives first; and one more barrier
+// at the end, which also keeps the search's registers free of spills.
+template <int E, bool kBarriers>
 __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& u, int unit,
                                             int tile, int m, bool valid, const float (&dd)[E + 1],
-                                            const int (&nb)[E + 1], double* stage, int* s_last) {
+                                            const int (&nb)[E + 1], double* stage, int k0) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int n_m = u.n_m;
   const int off = (E - 1) * u.tau;
@@ -283,10 +315,12 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
     const float di = __fsqrt_rn(dd[s]);
     w[s] = fmaxf((d1 > 0.f) ? expf(-__fdiv_rn(di, d1)) : ((di == 0.f) ? 1.f : 0.f), u.wfloor);
     usum = __fadd_rn(usum, w[s]);
-    // an unfilled slot (only possible with non-finite device input) reads in bounds
+    // an unfilled slot (only possible with non-finite device input) reads, and
+    // is reported, in bounds
     nbc[s] = min(max(nb[s], 0), n_m - 1);
   }
-  __syncthreads();  // every thread is done with the search's shared memory
+  if (kBarriers) __syncthreads();  // every thread is done with the search's shared memory
+  const int red = tile & (kThreads / 32 - 1);  // this tile's reducer warp
 
   for (int t = 0; t < u.n_targets; ++t) {
     const TargetDesc tg = p.targets[u.tgt_off + t];
@@ -299,43 +333,24 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
       if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
       if (p.dbg_nbr) {
 #pragma unroll
-        for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nb[s];
+        for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nbc[s];
       }
     }
-    // Double-buffered staging: warp 0 reduces target t while the others
-    // predict target t+1.  The barrier of target t+1 is reached by warp 0
-    // only after it has finished with target t-1's buffer.
-    double* buf = stage + (t & 1) * 2 * kQT;
+    double* buf = stage + ((k0 + t) & 1) * 2 * kQT;
     buf[tid] = valid ? (double)si[m + off] : 0.0;
     buf[kQT + tid] = valid ? (double)xhat : 0.0;
     __syncthreads();
-    if (warp == 0)
+    if (warp == red)
       tile_moments(buf, buf + kQT, nq, p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile));
   }
 
-  // The last tile of this realization to finish merges every target's tile
-  // moments (lane 0 of warp 0 wrote them all, before the fence).
-  if (tid == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(&p.unit_done[unit], 1u);
-    *s_last = (prev == (unsigned)(u.n_tiles - 1)) ? 1 : 0;
-  }
-  __syncthreads();
-  if (*s_last) {
-    __threadfence();
-    for (int t = warp; t < u.n_targets; t += kThreads / 32) {
-      const double r = merge_moments(p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles),
-                                     u.n_tiles);
-      if ((tid & 31) == 0) p.rho[p.targets[u.tgt_off + t].out_idx] = r;
-    }
-    if (tid == 0) p.unit_done[unit] = 0u;  // ready for the next run
-  }
-  __syncthreads();
+  if (warp == red) complete_tile(p, u, unit);
+  if (kBarriers) __syncthreads();
 }
 
 template <int E, int V>
 __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, int tile,
-                             unsigned char* smem, int* s_last) {
+                             unsigned char* smem) {
   constexpr int K = E + 1;  // the window keeps m itself out, so E+1 slots suffice
   constexpr int EP = TileShape<E>::EP;
   constexpr int LT = TileShape<E>::LT;
@@ -513,7 +528,7 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
     nb[s] = key_index(ku[s]);
   }
   // the library tile in shared memory is free once every thread is in the epilogue
-  finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, reinterpret_cast<double*>(smem), s_last);
+  finish_tile<E, true>(p, u, unit, tile, m, valid, dd, nb, reinterpret_cast<double*>(smem), 0);
 }
 
 // --------------------------------------------------------------------------
@@ -543,7 +558,7 @@ constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
 
 template <int E>
 __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
-                                   unsigned char* smem, int* s_last) {
+                                   unsigned char* smem) {
   const int tid = threadIdx.x;
   const int n_m = u.n_m, L = u.L, tau = u.tau, R = u.table_R, W = u.theiler;
   const int off = (E - 1) * tau;
@@ -634,13 +649,15 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
 #pragma unroll
     for (int s2 = 0; s2 <= E; ++s2)
       dd[s2] = valid ? d2_point<E>(sj, off, tau, q, max(nb[s2], 0)) : 0.f;
-    finish_tile<E>(p, u, unit, tile, m, valid, dd, nb, stage, s_last);
+    finish_tile<E, false>(p, u, unit, tile, m, valid, dd, nb, stage,
+                          (tile - tile0) * u.n_targets);
   }
 }
 
+template <int E>
 __global__ void __launch_bounds__(kThreads, 3) knn_table_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_item, s_last;
+  __shared__ int s_item;
   for (int64_t round = 0;; ++round) {
     if (p.persistent) {
       if (threadIdx.x == 0) s_item = (int)atomicAdd(p.item_counter, 1u);
@@ -651,22 +668,18 @@ __global__ void __launch_bounds__(kThreads, 3) knn_table_kernel(KnnParams p) {
     if ((int64_t)it >= p.n_items) break;
     const WorkItem w = p.items[it];
     const UnitDesc u = p.units[w.unit];
-    switch (u.E) {
-#define CCM_TT(EV) \
-  case EV: process_table_item<EV>(p, u, w.unit, w.tile, smem, &s_last); break;
-      CCM_TT(1) CCM_TT(2) CCM_TT(3) CCM_TT(4) CCM_TT(5)
-      CCM_TT(6) CCM_TT(7) CCM_TT(8) CCM_TT(9) CCM_TT(10)
-#undef CCM_TT
-      default:
-        if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
+    if (u.E != E) {
+      if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
+      continue;
     }
+    process_table_item<E>(p, u, w.unit, w.tile, smem);
   }
 }
 
 template <int E>
 __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_item, s_last;
+  __shared__ int s_item;
   for (int64_t round = 0;; ++round) {
     if (p.persistent) {
       if (threadIdx.x == 0) s_item = (int)atomicAdd(p.item_counter, 1u);
@@ -682,9 +695,9 @@ __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
       continue;
     }
     if (p.variant[E] == 1)
-      process_tile<E, 1>(p, u, w.unit, w.tile, smem, &s_last);
+      process_tile<E, 1>(p, u, w.unit, w.tile, smem);
     else
-      process_tile<E, 0>(p, u, w.unit, w.tile, smem, &s_last);
+      process_tile<E, 0>(p, u, w.unit, w.tile, smem);
   }
 }
 
@@ -696,27 +709,42 @@ size_t knn_table_smem(int max_nm) {
   return (size_t)kStageBytes + kHitBytes + (size_t)((max_nm + 31) / 32) * 4 + 16;
 }
 
+#define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+
 cudaError_t knn_table_prepare() {
   // the largest bitmap any plan may need (manifolds up to kTableMaxNm points);
   // set once, so that plans of different sizes never lower it for each other
-  return cudaFuncSetAttribute(knn_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)knn_table_smem(kTableMaxNm));
+#define CCM_TPREP(EV)                                                             \
+  {                                                                               \
+    const cudaError_t e = cudaFuncSetAttribute(                                   \
+        knn_table_kernel<EV>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+        (int)knn_table_smem(kTableMaxNm));                                        \
+    if (e != cudaSuccess) return e;                                               \
+  }
+  CCM_FOR_E(CCM_TPREP)
+#undef CCM_TPREP
+  return cudaSuccess;
 }
 
 cudaError_t knn_table_occupancy(int max_nm, int* ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_table_kernel, kThreads,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_table_kernel<kMaxE>, kThreads,
                                                        knn_table_smem(max_nm));
 }
 
-cudaError_t launch_knn_table(const KnnParams& p, int max_nm, int grid, cudaStream_t s) {
-  knn_table_kernel<<<grid, kThreads, knn_table_smem(max_nm), s>>>(p);
-  return cudaGetLastError();
+cudaError_t launch_knn_table(const KnnParams& p, int E, int max_nm, int grid, cudaStream_t s) {
+#define CCM_TLAUNCH(EV)                                                           \
+  if (E == EV) {                                                                  \
+    knn_table_kernel<EV><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p);       \
+    return cudaGetLastError();                                                    \
+  }
+  CCM_FOR_E(CCM_TLAUNCH)
+#undef CCM_TLAUNCH
+  return cudaErrorInvalidValue;
 }
 int knn_queries_per_thread() { return 1; }
 size_t knn_smem_bytes(int, int) { return kSmemBytes; }
 
 // One kernel per E (each keeps all its registers for that E's lists).
-#define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
 cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s) {
 #define CCM_LAUNCH(EV)                                                          \

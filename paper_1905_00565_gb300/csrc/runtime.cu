@@ -140,6 +140,8 @@ struct UnitList {
   std::vector<double> item_cost;
   int64_t e_first[kMaxE + 1] = {};    // items of E: e_count[E] from index e_first[E]
   int64_t e_count[kMaxE + 1] = {};
+  int64_t te_first[kMaxE + 1] = {};   // the same for the table items
+  int64_t te_count[kMaxE + 1] = {};
   std::vector<OrderJob> orders;       // one per (job, library variable, E, tau)
   std::vector<TableJob> tables;       // distance indexing tables to build
   std::vector<WorkItem> items_table;  // work items of units that read a table
@@ -392,19 +394,27 @@ void sort_items(UnitList* ul) {
       at += ul->e_count[E];
     }
   }
-  // Table items: grouped by table (a table of 20-80 MB stays in L2 while its
-  // realizations run), larger items first within a table.
+  // Table items: grouped by E (one launch per E), then by table (a table of
+  // 5-30 MB stays in L2 while its realizations run), larger items first.
   std::vector<int64_t> order(ul->items_table.size());
   for (size_t q = 0; q < order.size(); ++q) order[q] = (int64_t)q;
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-    const int64_t ta = ul->units[(size_t)ul->items_table[(size_t)a].unit].table_off;
-    const int64_t tb = ul->units[(size_t)ul->items_table[(size_t)b].unit].table_off;
-    if (ta != tb) return ta < tb;
+    const UnitDesc& ua = ul->units[(size_t)ul->items_table[(size_t)a].unit];
+    const UnitDesc& ub = ul->units[(size_t)ul->items_table[(size_t)b].unit];
+    if (ua.E != ub.E) return ua.E > ub.E;
+    if (ua.table_off != ub.table_off) return ua.table_off < ub.table_off;
     return ul->item_cost_table[(size_t)a] > ul->item_cost_table[(size_t)b];
   });
   std::vector<WorkItem> sorted(order.size());
   for (size_t q = 0; q < order.size(); ++q) sorted[q] = ul->items_table[(size_t)order[q]];
   ul->items_table.swap(sorted);
+  for (int E = 0; E <= kMaxE; ++E) ul->te_first[E] = ul->te_count[E] = 0;
+  for (const WorkItem& w : ul->items_table) ++ul->te_count[ul->units[(size_t)w.unit].E];
+  int64_t at = 0;
+  for (int E = kMaxE; E >= 1; --E) {
+    ul->te_first[E] = at;
+    at += ul->te_count[E];
+  }
 }
 
 // Device arena layout for a unit list.
@@ -430,7 +440,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.done = take(sizeof(uint32_t) * ul.units.size());
   a.rho = take(sizeof(double) * (size_t)n_rho);
   a.err = take(sizeof(int32_t));
-  a.counter = take((kMaxE + 1) * sizeof(uint32_t));  // [0] table items, [E] brute force of E
+  a.counter = take(2 * (kMaxE + 1) * sizeof(uint32_t));  // [E] brute force, [kMaxE+1+E] table
   a.scratch = take(sizeof(float) * (size_t)scratch_floats);
   a.order = take(sizeof(int32_t) * (size_t)ul.order_total);
   a.order_scratch = take(sizeof(unsigned long long) * (size_t)ul.order_scratch_total);
@@ -623,7 +633,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                      : cudaEventRecord(e, s);
   };
   CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
-  CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, (kMaxE + 1) * sizeof(uint32_t), s));
+  CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, 2 * (kMaxE + 1) * sizeof(uint32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
   if (ev) CCM_CUDA(record(ev[0]));
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
@@ -657,13 +667,14 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
     CCM_CUDA(launch_knn(ke, E, g, s));
   }
   if (ev) CCM_CUDA(record(ev[3]));
-  if (!ul.items_table.empty()) {
+  for (int E = kMaxE; E >= 1; --E) {
+    if (ul.te_count[E] == 0) continue;
     KnnParams kt = kp;
-    kt.items = reinterpret_cast<const WorkItem*>(base + ar.items_table);
-    kt.n_items = (int64_t)ul.items_table.size();
-    kt.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter);
-    const int g = persistent ? grid_table : (int)ul.items_table.size();
-    CCM_CUDA(launch_knn_table(kt, ul.max_nm, g, s));
+    kt.items = reinterpret_cast<const WorkItem*>(base + ar.items_table) + ul.te_first[E];
+    kt.n_items = ul.te_count[E];
+    kt.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter) + (kMaxE + 1) + E;
+    const int g = persistent ? grid_table : (int)std::min<int64_t>(ul.te_count[E], 0x7fffffff);
+    CCM_CUDA(launch_knn_table(kt, E, ul.max_nm, g, s));
   }
   if (ev) CCM_CUDA(record(ev[4]));
   return CCM_OK;
@@ -921,11 +932,11 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.flop_count = pl->ul.flops;
   in.brute_flop_count = pl->ul.brute_flops;
   in.table_bytes = pl->ul.table_elem() * (size_t)pl->ul.table_total;
-  // launches of one ccm_run: order, tables, sampler, one brute-force kernel
-  // per E present, the table scan
-  in.launches_per_run = 2 + (pl->ul.tables.empty() ? 0 : 1) +
-                        (pl->ul.items_table.empty() ? 0 : 1);
-  for (int E = 1; E <= kMaxE; ++E) in.launches_per_run += (pl->ul.e_count[E] > 0) ? 1 : 0;
+  // launches of one ccm_run: order, tables, sampler, one brute-force and one
+  // table-scan kernel per E present
+  in.launches_per_run = 2 + (pl->ul.tables.empty() ? 0 : 1);
+  for (int E = 1; E <= kMaxE; ++E)
+    in.launches_per_run += (pl->ul.e_count[E] > 0 ? 1 : 0) + (pl->ul.te_count[E] > 0 ? 1 : 0);
   *out = pl.release();
   return CCM_OK;
 }
