@@ -552,9 +552,12 @@ __device__ __forceinline__ float d2_point(const float* sj, int off, int tau, con
 }
 
 // Shared memory of the table kernel: the epilogue's staging buffer, the hits
-// of every query (slot-major, one column per thread), then the bitmap.
+// of every query (slot-major, one column per thread), then the library
+// membership map: one byte per manifold point when the manifold has at most
+// kByteMapMax points (a load and a compare per table entry), else one bit.
 constexpr int kStageBytes = 4 * kQT * 8;
 constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
+constexpr int kByteMapMax = 32768;
 
 template <int E>
 __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
@@ -566,22 +569,23 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
   const int32_t* lib = p.lib + u.lib_off;
   double* stage = reinterpret_cast<double*>(smem);
   int32_t* s_hit = reinterpret_cast<int32_t*>(smem + kStageBytes);
-  uint32_t* bm = reinterpret_cast<uint32_t*>(smem + kStageBytes + kHitBytes);
-  const int words = (n_m + 31) >> 5;
-  // Library membership, one bit per manifold point, once for the item's tiles.
-  __syncthreads();  // the previous item's readers of bm are done
-  for (int w = tid; w < words; w += kThreads) bm[w] = 0u;
+  unsigned char* map = smem + kStageBytes + kHitBytes;
+  const bool bytes = n_m <= kByteMapMax;
+  const int words = bytes ? (n_m + 3) >> 2 : (n_m + 31) >> 5;  // 32-bit words of the map
+  uint32_t* mw = reinterpret_cast<uint32_t*>(map);
+  // Library membership, once for the item's tiles.
+  __syncthreads();  // the previous item's readers of the map are done
+  for (int w = tid; w < words; w += kThreads) mw[w] = 0u;
   __syncthreads();
   for (int a = tid; a < L; a += kThreads) {
     const int l = lib[a];
-    atomicOr(&bm[l >> 5], 1u << (l & 31));
+    if (bytes) map[l] = 1;
+    else atomicOr(&mw[l >> 5], 1u << (l & 31));
   }
   __syncthreads();
 
   const int tile1 = min(u.n_tiles, tile0 + kTableChunk);
-  const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u.table_off;
-  const int32_t* t32 = static_cast<const int32_t*>(p.table) + u.table_off;
-  constexpr int kFlight = 8;  // table loads in flight per lane
+  const int groups = R >> 2;  // groups of four ranks
   for (int tile = tile0; tile < tile1; ++tile) {
     const int pos = tile * kQT + tid;
     const bool valid = pos < n_m;
@@ -590,28 +594,45 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
 #pragma unroll
     for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
 
-    // Walk the row: the first E+1 members (other than m) are the neighbours,
-    // in (distance, index) order.  A hit goes to this thread's column of s_hit.
+    // Walk the row: the first E+1 members (outside the window) are the
+    // neighbours, in (distance, index) order.  Hits go to this thread's column
+    // of s_hit.  Two groups (eight ranks) per step, loaded together.
     int found = valid ? 0 : E + 1;
-    const int col = valid ? pos : 0;
-    int r = 0;
-    while (__any_sync(kFull, found <= E && r < R)) {
-      int idx[kFlight];
-#pragma unroll
-      for (int c = 0; c < kFlight; ++c) {
-        const bool want = found <= E && r + c < R;
-        const int64_t o = (int64_t)(r + c) * n_m + col;
-        idx[c] = !want ? -1 : (p.table_u16 ? (int)__ldg(t16 + o) : __ldg(t32 + o));
+    const int64_t col = (int64_t)(valid ? pos : 0) * 4;
+    auto take = [&](int x) {
+      const bool member = bytes ? map[x] != 0 : ((mw[x >> 5] >> (x & 31)) & 1u) != 0;
+      if (found <= E && member && abs(x - m) > W) {
+        s_hit[found * kThreads + tid] = x;
+        ++found;
       }
-#pragma unroll
-      for (int c = 0; c < kFlight; ++c) {
-        const int x = idx[c];
-        if (found <= E && x >= 0 && abs(x - m) > W && ((bm[x >> 5] >> (x & 31)) & 1u)) {
-          s_hit[found * kThreads + tid] = x;
-          ++found;
+    };
+    for (int g = 0; __any_sync(kFull, found <= E && g < groups); g += 2) {
+      const bool w0 = found <= E && g < groups, w1 = found <= E && g + 1 < groups;
+      if (p.table_u16) {
+        const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u.table_off + col;
+        const uint2 v0 = w0 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)g * 4 * n_m))
+                            : make_uint2(0xffffffffu, 0xffffffffu);
+        const uint2 v1 = w1 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)(g + 1) * 4 * n_m))
+                            : make_uint2(0xffffffffu, 0xffffffffu);
+        if (w0) {
+          take(v0.x & 0xffffu); take(v0.x >> 16); take(v0.y & 0xffffu); take(v0.y >> 16);
+        }
+        if (w1) {
+          take(v1.x & 0xffffu); take(v1.x >> 16); take(v1.y & 0xffffu); take(v1.y >> 16);
+        }
+      } else {
+        const int32_t* t32 = static_cast<const int32_t*>(p.table) + u.table_off + col;
+        const int4 v0 = w0 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)g * 4 * n_m))
+                           : make_int4(0, 0, 0, 0);
+        const int4 v1 = w1 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)(g + 1) * 4 * n_m))
+                           : make_int4(0, 0, 0, 0);
+        if (w0) {
+          take(v0.x); take(v0.y); take(v0.z); take(v0.w);
+        }
+        if (w1) {
+          take(v1.x); take(v1.y); take(v1.z); take(v1.w);
         }
       }
-      r += kFlight;
     }
     int nb[E + 1];
     if (found > E) {
@@ -706,7 +727,11 @@ __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
 int knn_block_threads() { return kThreads; }
 
 size_t knn_table_smem(int max_nm) {
-  return (size_t)kStageBytes + kHitBytes + (size_t)((max_nm + 31) / 32) * 4 + 16;
+  // every manifold of the launch fits: bytes up to kByteMapMax points, bits above
+  const size_t bits = (size_t)((max_nm + 31) / 32) * 4;
+  const size_t map = (max_nm <= kByteMapMax) ? (size_t)(max_nm + 3) / 4 * 4
+                                             : (bits > (size_t)kByteMapMax ? bits : kByteMapMax);
+  return (size_t)kStageBytes + kHitBytes + map + 16;
 }
 
 #define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)

@@ -259,7 +259,8 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
           // the window removes up to 2W more of the nearest points from every row
           int64_t R = (int64_t)std::ceil(safety * (E + 2) * (double)n_m / (double)lmin) + 64 +
                       2 * (int64_t)pc.theiler;
-          R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR), n_m);
+          // whole groups of four ranks (the table's layout)
+          R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR), n_m / 4 * 4);
           const double bytes = (double)n_m * (double)R * (n_m < 65536 ? 2.0 : 4.0);
           if (table_bytes + bytes > table_cap_bytes) continue;
           table_bytes += bytes;

@@ -12,9 +12,11 @@
 // members (the query itself skipped) are exactly its E+1 nearest library
 // neighbours: restricting a total order to a subset keeps its order.
 //
-// Layout: table[table_off + r * n_m + pos], so that the 32 consecutive query
-// positions of a warp read one rank with one coalesced access; 16-bit entries
-// when every manifold of the plan has fewer than 65536 points, else 32-bit.
+// Layout: ranks in groups of four, table[table_off + (r/4) * 4*n_m + pos*4 +
+// r%4], so that one 8-byte (16-bit entries) or 16-byte (32-bit) load gives a
+// query four consecutive ranks and the 32 consecutive query positions of a
+// warp read one group with one coalesced access; 16-bit entries when every
+// manifold of the plan has fewer than 65536 points, else 32-bit.
 //
 // Build: one warp per query position.  Three radix passes (11, 11, 10 bits) of
 // a histogram over the FP32 bit patterns of all N_m squared distances find the
@@ -147,12 +149,15 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
       __syncwarp();
     }
   }
+  const int64_t base = jb.table_off + (int64_t)pos * 4;
   if (u16) {
-    uint16_t* out = static_cast<uint16_t*>(table) + jb.table_off + pos;
-    for (int r = lane; r < R; r += 32) out[(int64_t)r * n_m] = (uint16_t)(keys[r] & 0xffffu);
+    uint16_t* out = static_cast<uint16_t*>(table) + base;
+    for (int r = lane; r < R; r += 32)
+      out[(int64_t)(r >> 2) * 4 * n_m + (r & 3)] = (uint16_t)(keys[r] & 0xffffu);
   } else {
-    int32_t* out = static_cast<int32_t*>(table) + jb.table_off + pos;
-    for (int r = lane; r < R; r += 32) out[(int64_t)r * n_m] = (int32_t)(keys[r] & 0xffffffffu);
+    int32_t* out = static_cast<int32_t*>(table) + base;
+    for (int r = lane; r < R; r += 32)
+      out[(int64_t)(r >> 2) * 4 * n_m + (r & 3)] = (int32_t)(keys[r] & 0xffffffffu);
   }
   __syncwarp();
 }
