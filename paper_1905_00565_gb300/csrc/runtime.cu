@@ -163,8 +163,13 @@ struct UnitList {
 // Measured on GB300 (N_m = 10^4) the two break even near L = 900 for E = 1
 // and L = 450 for E = 10, i.e. L ~ sqrt(190*N_m/(E+1)); below that brute
 // force is faster.  The last term keeps R = 4(E+2)N_m/L + 64 within kTableMaxR.
+// CCM_TABLE_CROSSOVER replaces the 190 (tuning and measurement only).
 double table_min_L(int32_t E, int64_t n_m) {
-  return std::max({256.0, std::ceil(std::sqrt(190.0 * (double)n_m / (double)(E + 1))),
+  static const double c = [] {
+    const char* env = getenv("CCM_TABLE_CROSSOVER");
+    return env ? std::max(0.0, atof(env)) : 190.0;
+  }();
+  return std::max({256.0, std::ceil(std::sqrt(c * (double)n_m / (double)(E + 1))),
                    std::ceil(4.0 * (E + 2) * (double)n_m / (double)(kTableMaxR - 64))});
 }
 
