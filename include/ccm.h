@@ -72,10 +72,10 @@ typedef enum {
                                       per-(variable, E, tau) tables built in the same run,
                                       where that is faster and the tables fit a quarter of
                                       the context budget; results are identical either way.
-                                      Tuning knobs (environment, read once): CCM_TABLE_SAFETY
-                                      (default 4: table row length over the expected scan
-                                      length) and CCM_TABLE_CROSSOVER (default 190: tables
-                                      for L >= sqrt(c*N_m/(E+1))) */
+                                      Tuning knobs (environment): CCM_TABLE_SAFETY (read at
+                                      each ccm_plan; default 4: table row length over the
+                                      expected scan length) and CCM_TABLE_CROSSOVER (read
+                                      once; default 190: tables for L >= sqrt(c*N_m/(E+1))) */
 
 typedef struct {
   int32_t n_series;        /* V >= 2 series, each of length n */
