@@ -599,38 +599,45 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
     // of s_hit.  Two groups (eight ranks) per step, loaded together.
     int found = valid ? 0 : E + 1;
     const int64_t col = (int64_t)(valid ? pos : 0) * 4;
-    auto take = [&](int x) {
-      const bool member = bytes ? map[x] != 0 : ((mw[x >> 5] >> (x & 31)) & 1u) != 0;
-      if (found <= E && member && abs(x - m) > W) {
-        s_hit[found * kThreads + tid] = x;
-        ++found;
-      }
+    auto member = [&](int x) -> uint32_t {
+      return bytes ? (uint32_t)map[x] : ((mw[x >> 5] >> (x & 31)) & 1u);
     };
     for (int g = 0; __any_sync(kFull, found <= E && g < groups); g += 2) {
       const bool w0 = found <= E && g < groups, w1 = found <= E && g + 1 < groups;
+      int x[8];  // ranks 4g .. 4g+7 of this query's row (index 0 when not loaded)
       if (p.table_u16) {
         const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u.table_off + col;
         const uint2 v0 = w0 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)g * 4 * n_m))
-                            : make_uint2(0xffffffffu, 0xffffffffu);
+                            : make_uint2(0u, 0u);
         const uint2 v1 = w1 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)(g + 1) * 4 * n_m))
-                            : make_uint2(0xffffffffu, 0xffffffffu);
-        if (w0) {
-          take(v0.x & 0xffffu); take(v0.x >> 16); take(v0.y & 0xffffu); take(v0.y >> 16);
-        }
-        if (w1) {
-          take(v1.x & 0xffffu); take(v1.x >> 16); take(v1.y & 0xffffu); take(v1.y >> 16);
-        }
+                            : make_uint2(0u, 0u);
+        x[0] = v0.x & 0xffffu; x[1] = v0.x >> 16; x[2] = v0.y & 0xffffu; x[3] = v0.y >> 16;
+        x[4] = v1.x & 0xffffu; x[5] = v1.x >> 16; x[6] = v1.y & 0xffffu; x[7] = v1.y >> 16;
       } else {
         const int32_t* t32 = static_cast<const int32_t*>(p.table) + u.table_off + col;
         const int4 v0 = w0 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)g * 4 * n_m))
                            : make_int4(0, 0, 0, 0);
         const int4 v1 = w1 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)(g + 1) * 4 * n_m))
                            : make_int4(0, 0, 0, 0);
-        if (w0) {
-          take(v0.x); take(v0.y); take(v0.z); take(v0.w);
-        }
-        if (w1) {
-          take(v1.x); take(v1.y); take(v1.z); take(v1.w);
+        x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+        x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+      }
+      // library members among the eight ranks, one bit each; then the members
+      // in rank order (most groups hold none)
+      uint32_t bits = 0u;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) bits |= member(x[c]) << c;
+      bits &= (w0 ? 0x0fu : 0u) | (w1 ? 0xf0u : 0u);
+      while (bits != 0u && found <= E) {
+        const int c = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const int lo = (c & 1) ? x[1] : x[0], hi = (c & 1) ? x[3] : x[2];
+        const int lo2 = (c & 1) ? x[5] : x[4], hi2 = (c & 1) ? x[7] : x[6];
+        const int q4 = (c & 2) ? hi : lo, q4b = (c & 2) ? hi2 : lo2;
+        const int xc = (c & 4) ? q4b : q4;
+        if (abs(xc - m) > W) {
+          s_hit[found * kThreads + tid] = xc;
+          ++found;
         }
       }
     }
