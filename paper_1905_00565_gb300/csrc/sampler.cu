@@ -10,11 +10,12 @@
 //
 // One CTA per unit.  The high halves h(m) are computed once into shared memory
 // (or recomputed per pass when N_m is too large), an 8-bit radix select over
-// four passes finds the L-th smallest key (h*, and how many of the h == h*
-// points, smallest m first, are taken).  An in-order block compaction over m
-// finds the largest tie taken (and writes the checking copy, ascending m); a
-// second one over the unit's query order writes the library in query order,
-// the order the neighbour search visits it in (spatially coherent runs).
+// four passes (bins scanned by one warp) finds the L-th smallest key (h*, and
+// how many of the h == h* points, smallest m first, are taken; when some ties
+// are left out, one warp finds the last tie taken).  A warp-by-warp stable
+// compaction over the unit's query order writes the library in query order,
+// the order the neighbour search visits it in (spatially coherent runs); the
+// checking copy is compacted in ascending m.
 #include "ccm_internal.h"
 
 namespace ccm {
@@ -48,32 +49,38 @@ __device__ __forceinline__ uint32_t key_hi(const UnitDesc& u, int m) {
   return (uint32_t)(philox_word0((uint64_t)m, (uint64_t)u.k, (uint64_t)u.L, c3, u.seed, 0) >> 32);
 }
 
-// Exclusive block scan of one uint32 per thread; returns the block total.
-__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* excl, uint32_t* warp_tot) {
+// Stable compaction of the members among positions [0, n) by the whole block,
+// warp by warp: warp w walks its contiguous segment 32 positions at a time
+// (coalesced reads), counts members with a ballot, and after a block scan of
+// the warp counts writes them in position order.  item(q) gives the manifold
+// point at position q; is_member(m) decides membership.
+template <typename Item, typename Member>
+__device__ uint32_t block_compact(int n, Item item, Member is_member, int32_t* out,
+                                  uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+  const int seg = ((n + nwarps - 1) / nwarps + 31) / 32 * 32;
+  const int q0 = min(n, warp * seg), q1 = min(n, q0 + seg);
+  uint32_t count = 0u;
+  for (int q = q0 + lane; q - lane < q1; q += 32) {
+    const bool mem = q < q1 && is_member(item(q));
+    count += __popc(__ballot_sync(0xffffffffu, mem));
   }
-  if (lane == 31) warp_tot[warp] = x;
+  if (lane == 0) s_warp[warp] = count;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t t = (lane < nwarps) ? warp_tot[lane] : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < nwarps) warp_tot[lane] = t;  // inclusive prefix of warp totals
+  uint32_t base = 0u, total = 0u;
+  for (int w = 0; w < nwarps; ++w) {
+    base += (w < warp) ? s_warp[w] : 0u;
+    total += s_warp[w];
   }
   __syncthreads();
-  const uint32_t before = (warp > 0) ? warp_tot[warp - 1] : 0u;
-  *excl = before + x - v;
-  const uint32_t total = warp_tot[nwarps - 1];
-  __syncthreads();
+  for (int q = q0 + lane; q - lane < q1; q += 32) {
+    const int m = q < q1 ? item(q) : 0;
+    const bool mem = q < q1 && is_member(m);
+    const unsigned bal = __ballot_sync(0xffffffffu, mem);
+    if (mem) out[base + __popc(bal & ((1u << lane) - 1u))] = m;
+    base += __popc(bal);
+  }
   return total;
 }
 
@@ -83,12 +90,13 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
   extern __shared__ uint32_t s_keys[];
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_warp[32];
-  __shared__ uint32_t s_prefix, s_rank;
+  __shared__ uint32_t s_prefix, s_rank, s_neq;
   __shared__ int s_mtie;
 
   const int64_t uidx = first_unit + blockIdx.x;
   const UnitDesc u = p.units[uidx];
   const int n_m = u.n_m, L = u.L;
+  const int lane = threadIdx.x & 31;
   if (L < 1 || L > n_m) {
     if (threadIdx.x == 0) atomicOr(p.err, kErrSampler);
     return;
@@ -99,7 +107,6 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
   if (threadIdx.x == 0) {
     s_prefix = 0u;
     s_rank = (uint32_t)L;  // 1-based rank still to find within the current prefix
-    s_mtie = -1;
   }
   uint32_t mask = 0u;
   for (int pass = 0; pass < 4; ++pass) {
@@ -112,15 +119,31 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
       if ((h & mask) == prefix) atomicAdd(&s_hist[(h >> shift) & 255u], 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t rank = s_rank, cum = 0u;
-      int b = 0;
-      for (; b < 256; ++b) {
-        if (cum + s_hist[b] >= rank) break;
-        cum += s_hist[b];
+    if (threadIdx.x < 32) {
+      // the bin holding rank s_rank: lane l sums bins 8l..8l+7, then a warp scan
+      const uint32_t rank = s_rank;
+      uint32_t mine = 0u;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) mine += s_hist[lane * 8 + b];
+      uint32_t incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      s_prefix = prefix | ((uint32_t)b << shift);
-      s_rank = rank - cum;
+      const unsigned hit = __ballot_sync(0xffffffffu, incl >= rank);
+      const int owner = __ffs(hit) - 1;  // exists: the histogram holds >= rank keys
+      if (lane == owner) {
+        uint32_t cum = incl - mine;
+        int b = lane * 8;
+        for (; b < lane * 8 + 7; ++b) {
+          if (cum + s_hist[b] >= rank) break;
+          cum += s_hist[b];
+        }
+        s_prefix = prefix | ((uint32_t)b << shift);
+        s_rank = rank - cum;
+        s_neq = s_hist[b];  // after the last pass: the keys equal to h*
+      }
     }
     mask |= 255u << shift;
     __syncthreads();
@@ -128,64 +151,47 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
   const uint32_t hstar = s_prefix;   // high half of the L-th smallest key
   const uint32_t take_ties = s_rank; // points with h == h* to take, smallest m first
 
-  // In-order compaction over contiguous chunks of m.
-  const int chunk = (n_m + blockDim.x - 1) / blockDim.x;
-  const int m0 = min(n_m, (int)threadIdx.x * chunk), m1 = min(n_m, m0 + chunk);
-  uint32_t n_less = 0u, n_tie = 0u;
-  for (int m = m0; m < m1; ++m) {
-    const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
-    n_less += (h < hstar);
-    n_tie += (h == hstar);
-  }
-  uint32_t tie_before;
-  block_exclusive_scan(n_tie, &tie_before, s_warp);
-  const uint32_t ties_here =
-      (tie_before >= take_ties) ? 0u : min(n_tie, take_ties - tie_before);
-  uint32_t out_before;
-  const uint32_t total = block_exclusive_scan(n_less + ties_here, &out_before, s_warp);
-  if (total != (uint32_t)L) {
-    if (threadIdx.x == 0) atomicOr(p.err, kErrSampler);
-    return;
-  }
-  uint32_t w = out_before, tie_seen = tie_before;
-  for (int m = m0; m < m1; ++m) {
-    const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
-    bool take = h < hstar;
-    if (h == hstar) {
-      take = tie_seen < take_ties;
-      if (take && tie_seen + 1 == take_ties) s_mtie = m;  // the last tie taken
-      ++tie_seen;
+  // Members: h < h*, or h == h* and m <= mtie (the last tie taken).  Almost
+  // always every tie is taken; otherwise warp 0 finds the take_ties-th tie.
+  if (threadIdx.x < 32) {
+    int mtie = 0x7fffffff;
+    if (take_ties < s_neq) {
+      uint32_t seen = 0u;
+      mtie = -1;
+      for (int m0 = 0; m0 < n_m && mtie < 0; m0 += 32) {
+        const int m = m0 + lane;
+        const bool tie = m < n_m && (kInSmem ? s_keys[m] : key_hi(u, m)) == hstar;
+        const unsigned bal = __ballot_sync(0xffffffffu, tie);
+        if (seen + __popc(bal) >= take_ties) {
+          unsigned b = bal;
+          for (uint32_t k = seen + 1; k < take_ties; ++k) b &= b - 1u;  // drop earlier ties
+          mtie = m0 + __ffs(b) - 1;
+        }
+        seen += __popc(bal);
+      }
     }
-    if (take) {
-      if (p.dbg_lib)  // checking copy, once per target of this library
-        for (int t = 0; t < u.n_targets; ++t)
-          p.dbg_lib[p.targets[u.tgt_off + t].lib_dbg_off + w] = m;
-      ++w;
-    }
+    if (lane == 0) s_mtie = mtie;
   }
   __syncthreads();
-  const int mtie = s_mtie;  // members: h < h*, or h == h* and m <= mtie
-
-  // The library in query order: compaction over contiguous chunks of positions.
-  const int32_t* ord = p.order + u.order_off;
-  uint32_t n_mem = 0u;
-  for (int q = m0; q < m1; ++q) {
-    const int m = ord[q];
+  const int mtie = s_mtie;
+  auto is_member = [&](int m) {
     const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
-    n_mem += (h < hstar || (h == hstar && m <= mtie));
-  }
-  uint32_t pos_before;
-  const uint32_t total2 = block_exclusive_scan(n_mem, &pos_before, s_warp);
-  if (total2 != (uint32_t)L) {
+    return h < hstar || (h == hstar && m <= mtie);
+  };
+  // The library in query order (the order the neighbour search visits it in).
+  const int32_t* ord = p.order + u.order_off;
+  const uint32_t total =
+      block_compact(n_m, [&](int q) { return ord[q]; }, is_member, p.lib + u.lib_off, s_warp);
+  if (total != (uint32_t)L) {  // not a permutation, or a lost tie: report, never guess
     if (threadIdx.x == 0) atomicOr(p.err, kErrSampler);
     return;
   }
-  int32_t* out = p.lib + u.lib_off;
-  w = pos_before;
-  for (int q = m0; q < m1; ++q) {
-    const int m = ord[q];
-    const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
-    if (h < hstar || (h == hstar && m <= mtie)) out[w++] = m;
+  if (p.dbg_lib) {  // checking copy in ascending m, once per target of this library
+    for (int t = 0; t < u.n_targets; ++t) {
+      __syncthreads();
+      block_compact(n_m, [](int q) { return q; }, is_member,
+                    p.dbg_lib + p.targets[u.tgt_off + t].lib_dbg_off, s_warp);
+    }
   }
 }
 
