@@ -45,6 +45,7 @@ using u64 = unsigned long long;
 
 constexpr int kThreads = 256;             // threads per CTA = queries per tile
 constexpr int kQT = kThreads;             // queries per tile (one per thread)
+static_assert((kQT & (kQT - 1)) == 0, "tile moments rely on a power-of-two tile");
 constexpr int kBuf = 16;                  // pending candidates per query
 constexpr int kCoordBytes = 40 * 1024;    // shared memory for one library tile + chunk boxes
 constexpr int kBoxBytes = 2 * 1024;       // chunk bounding boxes, at the end of that region
@@ -197,7 +198,11 @@ __device__ __forceinline__ void tile_moments(const double* xs, const double* ys,
   sx = warp_sum(sx);
   sy = warp_sum(sy);
   const double n = (double)nq;
-  const double mx = __ddiv_rn(sx, n), my = __ddiv_rn(sy, n);
+  // a full tile divides by 256 = 2^8: multiplying by 2^-8 gives the same bits
+  // and spares the FP64 pipe two divisions
+  const bool full = nq == kQT;
+  const double mx = full ? __dmul_rn(sx, 1.0 / kQT) : __ddiv_rn(sx, n);
+  const double my = full ? __dmul_rn(sy, 1.0 / kQT) : __ddiv_rn(sy, n);
   double sxx = 0.0, syy = 0.0, sxy = 0.0;
 #pragma unroll
   for (int c = 0; c < kPer; ++c) {
