@@ -48,7 +48,7 @@ UNIT = "realizations/s"
 # 2 flops per fused multiply-add x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 KNN_SRC = os.path.join(ROOT, "paper_1905_00565_gb300", "csrc", "knn_fused.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_fused_sweep_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_fused_default_traffic.json")
 
 
 def parse():
@@ -321,7 +321,9 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic_entry(),
-                         "traffic_unit": "DRAM bytes per step, all brute-force launches",
+                         "traffic_unit": "DRAM bytes per step, all brute-force launches "
+                                         "(ncu, scaled from an r=8 capture)",
+                         "algorithmic_bytes": "4L per realization (library indices) + 8 (rho)",
                          "kernel": "knn_fused_kernel<E> (brute force), one launch per E per step "
                                    "over the realizations below the table threshold; 3E FP32 "
                                    "flops per query-library pair, counting the pairs that exact "
