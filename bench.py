@@ -67,20 +67,43 @@ def parse():
     ap.add_argument("--scenario", default="", choices=["", "paper"],
                     help="paper: the paper's baseline scenario and its one-at-a-time "
                          "elasticity cases (context, not the bench line)")
+    ap.add_argument("--workload", default="sweep", choices=sorted(WORKLOADS),
+                    help="sweep (default: the benchmark line), or one of the other "
+                         "configurations: single, long, network")
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run every sweep cell with R realizations through ccm_run "
                          "twice (the small case for ncu captures) and exit")
     return ap.parse_args()
 
 
-def workload_config():
+WORKLOADS = {
+    "sweep": ("sweep_problem",
+              "ccm-sweep: coupled logistic map N=10000 (rx=3.8, ry=3.5, bxy=0.02, byx=0.1), "
+              "both directions, E=1..10, tau=1..4, 20 L log-spaced 100..9000, r=250"),
+    "single": ("plain_ccm_problem",
+               "ccm-single: coupled logistic map N=1000, both directions, E=2, tau=1, "
+               "L in {50,100,200,400,800}, r=100"),
+    "long": ("long_series_problem",
+             "ccm-long: weakly coupled logistic map (byx=0.01, bxy=0) + N(0, 0.01^2) noise, "
+             "N=100000, both directions, E=3..6, tau=1, L in {1k,5k,10k,25k,50k}, r=250"),
+    "network": ("network_problem",
+                "ccm-network: 64-variable coupled logistic network (5% couplings U(0,0.1)), "
+                "N=5000, all 4032 ordered pairs, E in {2,3,4}, tau=1, 8 L log-spaced "
+                "100..4500, r=250"),
+}
+
+
+def workload_problem(name):
+    from paper_1905_00565_gb300 import inputs as I
+    return getattr(I, WORKLOADS[name][0])()
+
+
+def workload_config(name, p):
     return {
-        "workload": "ccm-sweep: coupled logistic map N=10000 (rx=3.8, ry=3.5, bxy=0.02, "
-                    "byx=0.1), both directions, E=1..10, tau=1..4, 20 L log-spaced 100..9000, "
-                    "r=250",
-        "realizations": 400000,
-        "queries": 3995500000,
-        "pairs": 8451681150000,
+        "workload": WORKLOADS[name][1],
+        "realizations": p.n_units(),
+        "queries": p.queries(),
+        "pairs": p.pair_count(),
         "precision": "FP32 distances/selection/weights, FP64 rho moments",
     }
 
@@ -229,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    p = I.sweep_problem()
+    p = workload_problem(args.workload)
     ctx = ccm.ccm_context_create(local_rank)
     dev_flags = ccm.CCM_INPUT_ON_DEVICE | ccm.CCM_OUTPUT_ON_DEVICE
     plan = ccm.plan_problem(ctx, p, dev_flags)
@@ -303,7 +326,8 @@ def run_ours(args, rank, world, local_rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(), l2="256 MiB buffer written between timed steps",
+            "config": dict(workload_config(args.workload, p),
+                           l2="256 MiB buffer written between timed steps",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "queries_per_s": info["n_queries"] * world / (t_step / 1e3),
             "pairs_per_s": info["pair_count"] * world / (t_step / 1e3),
@@ -316,8 +340,8 @@ def run_ours(args, rank, world, local_rank):
                 "table_bytes": info["table_bytes"],
                 "brute_force_share_of_pairs": info["brute_flop_count"] / info["flop_count"]},
             "convergence": {"rows": n_rows, "converged_rows": int(conv_host["converged"].sum()),
-                            "test": "one-sided Jonckheere-Terpstra over the 20 L groups, "
-                                    "z > 1.645"},
+                            "test": f"one-sided Jonckheere-Terpstra over the {len(p.L)} L "
+                                    "groups, z > 1.645"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic_entry(),
@@ -557,6 +581,10 @@ def paper_scenario(args):
 
 def main():
     args = parse()
+    if args.workload in ("long", "network"):
+        # the plain comparator would take minutes here; the served stream is the
+        # same for every workload
+        args.no_plain = args.no_serving = True
     if args.profile_case:
         profile_case(args.profile_case)
         return
@@ -571,7 +599,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        p = I.sweep_problem()
+        p = workload_problem(args.workload)
         for _ in range(args.warmup):
             time_cpu_oracle(p, 16)
         vals = [time_cpu_oracle(p, args.cpu_sample_units) for _ in range(args.steps)]
@@ -580,7 +608,7 @@ def main():
                 "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * p.n_units() / v, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(),
+                "config": workload_config(args.workload, p),
                 "cpu_baseline": dict(vals[-1], value=v),
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -595,7 +623,7 @@ def main():
     # the CPU baseline runs before any GPU work so that its spawned workers start clean
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = time_cpu_oracle(I.sweep_problem(), args.cpu_sample_units)
+        cpu = time_cpu_oracle(workload_problem(args.workload), args.cpu_sample_units)
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
         out["cpu_baseline"] = cpu
