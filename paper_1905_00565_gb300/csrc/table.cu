@@ -18,11 +18,14 @@
 // warp read one group with one coalesced access; 16-bit entries when every
 // manifold of the plan has fewer than 65536 points, else 32-bit.
 //
-// Build: one warp per query position.  Three radix passes (11, 11, 10 bits) of
-// a histogram over the FP32 bit patterns of all N_m squared distances find the
-// R-th smallest value T and how many entries equal to T are taken; a fourth
-// pass collects every entry below T and, in index order, the first equal
-// ones; a bitonic sort in shared memory orders the R keys (bits << 32 | index).
+// Build: one warp per query position.  A histogram of the top 11 bits of the
+// FP32 bit patterns of all N_m squared distances finds the bin b1 holding rank
+// R; a second pass collects every entry below b1 (all of them belong to the
+// row) and the entries of b1, which are sorted by (bits, index) to take the
+// rest.  When b1 holds more than kTableBoundary entries, two more radix
+// passes (11, 10 bits) refine it to the exact R-th value T instead and a
+// pass collects the entries below T and, in index order, the first ties.  A
+// bitonic sort in shared memory orders the R keys (bits << 32 | index).
 #include <stdint.h>
 
 #include "ccm_internal.h"
@@ -31,6 +34,12 @@ namespace ccm {
 namespace {
 
 constexpr int kTableWarps = 8;  // query positions per CTA
+constexpr int kTableBoundary = 512;  // boundary-bin entries sorted directly (else refined)
+
+__host__ __device__ constexpr size_t table_warp_bytes(int rcap) {
+  return (size_t)(rcap + kTableBoundary) * 8 > 2048 * 4 ? (size_t)(rcap + kTableBoundary) * 8
+                                                        : (size_t)2048 * 4;
+}
 constexpr unsigned kFullMask = 0xffffffffu;
 
 // FP32 squared distance from query coordinates q to manifold point x, in the
@@ -49,93 +58,46 @@ __device__ __forceinline__ uint32_t d2_bits(const float* s, int off, int tau, co
   return __float_as_uint(acc);  // d2 >= +0: unsigned order is numeric order
 }
 
-template <int E>
-__device__ void build_row(const float* s, const TableJob& jb, int pos, const int32_t* order,
-                          void* table, int u16, uint32_t* hist, unsigned long long* keys) {
+// Warp-wide scan of a histogram in shared memory: the bin holding the
+// 1-based rank `rank`, and how many entries lie in the bins below it.
+__device__ __forceinline__ void select_bin(const uint32_t* hist, int nbins, int rank, int* bin_out,
+                                           uint32_t* before_out, uint32_t* count_out) {
   const int lane = threadIdx.x & 31;
-  const int n_m = jb.n_m, tau = jb.tau, off = (E - 1) * tau, R = jb.R;
-  const int m = order[jb.order_off + pos];
-  float q[E];
+  const int chunk = nbins / 32;  // each lane owns a contiguous chunk of bins
+  uint32_t mine = 0u;
+  for (int b = 0; b < chunk; ++b) mine += hist[lane * chunk + b];
+  uint32_t incl = mine;
 #pragma unroll
-  for (int e = 0; e < E; ++e) q[e] = s[m + off - e * tau];
-
-  // Radix select of the R-th smallest bit pattern (1-based rank).
-  uint32_t prefix = 0u, mask = 0u;
-  int rank = R;
-  for (int pass = 0; pass < 3; ++pass) {
-    const int sh = (pass == 0) ? 21 : (pass == 1) ? 10 : 0;
-    const int nbins = (pass == 2) ? 1024 : 2048;
-    const uint32_t dm = (uint32_t)nbins - 1u;
-    for (int b = lane; b < nbins; b += 32) hist[b] = 0u;
-    __syncwarp();
-    for (int x = lane; x < n_m; x += 32) {
-      const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
-      if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> sh) & dm], 1u);
-    }
-    __syncwarp();
-    // each lane owns a contiguous chunk of bins; scan the chunk sums
-    const int chunk = nbins / 32;
-    uint32_t mine = 0u;
-    for (int b = 0; b < chunk; ++b) mine += hist[lane * chunk + b];
-    uint32_t incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const unsigned hit = __ballot_sync(kFullMask, incl >= (uint32_t)rank);
-    const int owner = __ffs(hit) - 1;  // exists: the histogram holds >= rank entries
-    uint32_t before = __shfl_sync(kFullMask, incl - mine, owner);
-    int bin = 0;
-    if (lane == owner) {
-      uint32_t cum = before;
-      for (int b = 0; b < chunk; ++b) {
-        const uint32_t h = hist[lane * chunk + b];
-        if (cum + h >= (uint32_t)rank) {
-          bin = lane * chunk + b;
-          break;
-        }
-        cum += h;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned hit = __ballot_sync(kFullMask, incl >= (uint32_t)rank);
+  const int owner = __ffs(hit) - 1;  // exists: the histogram holds >= rank entries
+  uint32_t before = incl - mine, count = 0u;
+  int bin = 0;
+  if (lane == owner) {
+    for (int b = 0; b < chunk; ++b) {
+      const uint32_t h = hist[lane * chunk + b];
+      if (before + h >= (uint32_t)rank) {
+        bin = lane * chunk + b;
+        count = h;
+        break;
       }
-      before = cum;
+      before += h;
     }
-    bin = __shfl_sync(kFullMask, bin, owner);
-    before = __shfl_sync(kFullMask, before, owner);
-    prefix |= (uint32_t)bin << sh;
-    mask |= dm << sh;
-    rank -= (int)before;
-    __syncwarp();
   }
-  const uint32_t T = prefix;       // bit pattern of the R-th smallest squared distance
-  const int take_ties = rank;      // entries equal to T to take, lowest index first
-  const int n_less = R - take_ties;
+  *bin_out = __shfl_sync(kFullMask, bin, owner);
+  *before_out = __shfl_sync(kFullMask, before, owner);
+  *count_out = __shfl_sync(kFullMask, count, owner);
+}
 
-  // Collect in index order (deterministic slots): all below T, then the first
-  // take_ties equal to T.
-  int less_seen = 0, ties_seen = 0;
-  for (int base = 0; base < n_m; base += 32) {
-    const int x = base + lane;
-    const uint32_t bits = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
-    const bool less = (x < n_m) && bits < T;
-    const bool tie = (x < n_m) && bits == T;
-    const unsigned lm = __ballot_sync(kFullMask, less);
-    const unsigned tm = __ballot_sync(kFullMask, tie);
-    const unsigned below = (1u << lane) - 1u;
-    if (less) keys[less_seen + __popc(lm & below)] = ((unsigned long long)bits << 32) | (unsigned)x;
-    const int tr = ties_seen + __popc(tm & below);
-    if (tie && tr < take_ties)
-      keys[n_less + tr] = ((unsigned long long)bits << 32) | (unsigned)x;
-    less_seen += __popc(lm);
-    ties_seen += __popc(tm);
-  }
-  int rcap = 32;  // this row's sort size: the power of two at or above R
-  while (rcap < R) rcap <<= 1;
-  for (int i = R + lane; i < rcap; i += 32) keys[i] = ~0ull;
-  __syncwarp();
-  // bitonic sort of rcap keys, ascending
-  for (int k = 2; k <= rcap; k <<= 1) {
+// Ascending bitonic sort of n (a power of two) keys by one warp.
+__device__ __forceinline__ void warp_bitonic(unsigned long long* keys, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= n; k <<= 1) {
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int i = lane; i < rcap; i += 32) {
+      for (int i = lane; i < n; i += 32) {
         const int ixj = i ^ jj;
         if (ixj > i) {
           const unsigned long long a = keys[i], b = keys[ixj];
@@ -149,6 +111,101 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
       __syncwarp();
     }
   }
+}
+
+template <int E>
+__device__ void build_row(const float* s, const TableJob& jb, int pos, const int32_t* order,
+                          void* table, int u16, uint32_t* hist, unsigned long long* keys,
+                          unsigned long long* bnd) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below_lane = (1u << lane) - 1u;
+  const int n_m = jb.n_m, tau = jb.tau, off = (E - 1) * tau, R = jb.R;
+  const int m = order[jb.order_off + pos];
+  float q[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) q[e] = s[m + off - e * tau];
+  auto key_of = [](uint32_t bits, int x) { return ((unsigned long long)bits << 32) | (unsigned)x; };
+
+  // Pass 1: histogram of the top 11 bits (non-negative floats order like
+  // their bit patterns); the bin b1 holding rank R.
+  for (int b = lane; b < 2048; b += 32) hist[b] = 0u;
+  __syncwarp();
+  for (int x = lane; x < n_m; x += 32) atomicAdd(&hist[d2_bits<E>(s, off, tau, q, x) >> 21], 1u);
+  __syncwarp();
+  int b1;
+  uint32_t below1, in_b1;
+  select_bin(hist, 2048, R, &b1, &below1, &in_b1);
+  __syncwarp();
+
+  if (in_b1 <= (uint32_t)kTableBoundary) {
+    // Pass 2: every entry below b1 is a row entry; the entries of b1 are
+    // sorted and the first R - below1 of them complete the row.
+    uint32_t nl = 0u, nb = 0u;
+    for (int base = 0; base < n_m; base += 32) {
+      const int x = base + lane;
+      const uint32_t bits = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
+      const uint32_t bin = bits >> 21;
+      const bool lt = x < n_m && bin < (uint32_t)b1, eq = x < n_m && bin == (uint32_t)b1;
+      const unsigned lm = __ballot_sync(kFullMask, lt), em = __ballot_sync(kFullMask, eq);
+      if (lt) keys[nl + __popc(lm & below_lane)] = key_of(bits, x);
+      if (eq) bnd[nb + __popc(em & below_lane)] = key_of(bits, x);
+      nl += __popc(lm);
+      nb += __popc(em);
+    }
+    int p2 = 32;
+    while (p2 < (int)nb) p2 <<= 1;
+    for (int i = (int)nb + lane; i < p2; i += 32) bnd[i] = ~0ull;
+    __syncwarp();
+    warp_bitonic(bnd, p2);
+    for (int i = lane; i < R - (int)below1; i += 32) keys[below1 + i] = bnd[i];
+  } else {
+    // A crowded boundary bin: refine it with two more radix passes (11 and 10
+    // bits) to the exact R-th bit pattern T and how many entries equal to T
+    // are taken, then collect in index order.
+    uint32_t prefix = (uint32_t)b1 << 21, mask = 0x7ffu << 21;
+    int rank = R - (int)below1;
+    for (int pass = 1; pass < 3; ++pass) {
+      const int sh = (pass == 1) ? 10 : 0;
+      const int nbins = (pass == 2) ? 1024 : 2048;
+      const uint32_t dm = (uint32_t)nbins - 1u;
+      for (int b = lane; b < nbins; b += 32) hist[b] = 0u;
+      __syncwarp();
+      for (int x = lane; x < n_m; x += 32) {
+        const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
+        if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> sh) & dm], 1u);
+      }
+      __syncwarp();
+      int bin;
+      uint32_t before, cnt;
+      select_bin(hist, nbins, rank, &bin, &before, &cnt);
+      prefix |= (uint32_t)bin << sh;
+      mask |= dm << sh;
+      rank -= (int)before;
+      __syncwarp();
+    }
+    const uint32_t T = prefix;   // bit pattern of the R-th smallest squared distance
+    const int take_ties = rank;  // entries equal to T to take, lowest index first
+    const int n_less = R - take_ties;
+    int less_seen = 0, ties_seen = 0;
+    for (int base = 0; base < n_m; base += 32) {
+      const int x = base + lane;
+      const uint32_t bits = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
+      const bool less = (x < n_m) && bits < T;
+      const bool tie = (x < n_m) && bits == T;
+      const unsigned lm = __ballot_sync(kFullMask, less);
+      const unsigned tm = __ballot_sync(kFullMask, tie);
+      if (less) keys[less_seen + __popc(lm & below_lane)] = key_of(bits, x);
+      const int tr = ties_seen + __popc(tm & below_lane);
+      if (tie && tr < take_ties) keys[n_less + tr] = key_of(bits, x);
+      less_seen += __popc(lm);
+      ties_seen += __popc(tm);
+    }
+  }
+  int rcap = 32;  // this row's sort size: the power of two at or above R
+  while (rcap < R) rcap <<= 1;
+  for (int i = R + lane; i < rcap; i += 32) keys[i] = ~0ull;
+  __syncwarp();
+  warp_bitonic(keys, rcap);
   const int64_t base = jb.table_off + (int64_t)pos * 4;
   if (u16) {
     uint16_t* out = static_cast<uint16_t*>(table) + base;
@@ -170,15 +227,16 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
   const int warp = threadIdx.x >> 5;
   const int pos = blockIdx.x * kTableWarps + warp;
   if (pos >= jb.n_m) return;  // whole warp leaves; no block-wide barrier follows
-  // per warp: max(2048 histogram bins, rcap keys)
-  const size_t per_warp = (size_t)max(2048 * 4, rcap * 8);
-  unsigned char* mine = smem + warp * per_warp;
+  // per warp: the 2048 histogram bins, overlapping the rcap row keys and the
+  // kTableBoundary keys of the boundary bin
+  unsigned char* mine = smem + warp * table_warp_bytes(rcap);
   uint32_t* hist = reinterpret_cast<uint32_t*>(mine);
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(mine);
+  unsigned long long* bnd = keys + rcap;
   const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
   switch (jb.E) {
 #define CCM_TB(EV) \
-  case EV: build_row<EV>(s, jb, pos, order, table, u16, hist, keys); break;
+  case EV: build_row<EV>(s, jb, pos, order, table, u16, hist, keys, bnd); break;
     CCM_TB(1) CCM_TB(2) CCM_TB(3) CCM_TB(4) CCM_TB(5)
     CCM_TB(6) CCM_TB(7) CCM_TB(8) CCM_TB(9) CCM_TB(10)
 #undef CCM_TB
@@ -186,7 +244,7 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
   }
 }
 
-size_t table_smem(int rcap) { return (size_t)kTableWarps * (size_t)max(2048 * 4, rcap * 8); }
+size_t table_smem(int rcap) { return (size_t)kTableWarps * table_warp_bytes(rcap); }
 
 }  // namespace
 
