@@ -10,7 +10,9 @@
 // is an exact integer.  Non-finite rho (a realization with zero variance) are
 // left out.  Thread 0 forms E[J], Var[J] (no tie correction), z and the group
 // means (summed before sorting, in realization order) with explicit
-// round-to-nearest operations in the oracle's order.
+// round-to-nearest operations in a fixed order: group sizes summed in
+// increasing L, then E[J], Var[J] and z, so the result depends on nothing but
+// the row.
 #include <math.h>
 #include <stdint.h>
 
