@@ -147,7 +147,9 @@ ccm_status ccm_plan_destroy(ccm_plan_t* plan);
 
 ccm_status ccm_plan_get_info(const ccm_plan_t* plan, ccm_plan_info* info);
 
-/* Run the whole sweep: query order, distance indexing tables (unless
+/* Run the whole sweep: query order, observed-value tile moments (the target's
+ * mean and centred values per query tile of each (pair, E, tau), shared by
+ * every L and realization), distance indexing tables (unless
  * CCM_NO_TABLE or none pays off), library sampler, one persistent fused
  * kNN + simplex + rho kernel per E for the brute-force realizations and one
  * table-scan kernel for the rest; replayed from a CUDA graph after the first
@@ -171,14 +173,15 @@ ccm_status ccm_run(ccm_plan_t* plan, const float* series, double* rho, void* cud
 ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho,
                       const ccm_debug_out* dbg, void* cuda_stream);
 
-/* Device time of the preparation launches (query order, tables, sampler) and
- * of the neighbour-search launches (brute force + table scan) in the plan's
- * last completed ccm_run / ccm_run_ex (CUDA events recorded on the run's
- * stream around each launch).  Call after that run has finished. */
+/* Device time of the preparation launches (query order, observed moments,
+ * tables, sampler) and of the neighbour-search launches (brute force + table
+ * scan) in the plan's last completed ccm_run / ccm_run_ex (CUDA events
+ * recorded on the run's stream around each launch).  Call after that run has
+ * finished. */
 ccm_status ccm_plan_kernel_times(const ccm_plan_t* plan, double* sampler_ms, double* knn_ms);
 
-/* The same events per stage: stage_ms[0] query order + distance indexing
- * tables, [1] library sampler, [2] brute-force fused kernel, [3] table-scan
+/* The same events per stage: stage_ms[0] query order + observed-value tile
+ * moments + distance indexing tables, [1] library sampler, [2] brute-force fused kernel, [3] table-scan
  * fused kernel (0 when the stage launched nothing). */
 ccm_status ccm_plan_stage_times(const ccm_plan_t* plan, double* stage_ms /* [4] */);
 
@@ -221,9 +224,8 @@ ccm_status ccm_job_times(ccm_context* ctx, uint64_t ticket, double* submit_s, do
  * d_series: device [n_series][n] FP32 (not checked for non-finite values);
  * d_rho: device [r] FP64, written in stream order.  All scratch lives in one
  * fixed 16 MiB device array held by every GPU that loads the library until
- * exit; a cell needing more (about r*L*4 + r*ceil(N_m/256)*56 + r*150 +
- * N_m*4 bytes)
- * returns CCM_ETOOLARGE with a message and runs nothing.  Nothing is
+ * exit; a cell needing more (about r*L*4 + r*ceil(N_m/256)*56 + r*160 +
+ * N_m*4 + ceil(N_m/256)*2112 bytes) returns CCM_ETOOLARGE with a message and runs nothing.  Nothing is
  * allocated.  The first call on a device (with that device current) finds
  * the array's address and sets kernel attributes; make it before any stream
  * capture.  Every call reuses the same array: calls that overlap on the GPU
@@ -256,7 +258,9 @@ typedef struct {
  * (rho is device memory), CCM_OUTPUT_ON_DEVICE (out is device memory); host
  * buffers are staged through temporary device memory.  Limits: 2 <= n_L <= 64,
  * n_L*r <= 24576.  cuda_stream as in ccm_run (NULL: blocks until done).
- * Results equal the oracle's bit for bit (exact integer J, fixed FP64 order). */
+ * J is an exact integer and every FP64 step a round-to-nearest operation in a
+ * fixed order (group means in realization order, sizes in increasing L), so
+ * the result depends on nothing but the row. */
 ccm_status ccm_convergence(ccm_context* ctx, const double* rho, int64_t n_rows, int32_t n_L,
                            const int64_t* L, int32_t r, double z_crit,
                            ccm_convergence_t* out, uint32_t flags, void* cuda_stream);

@@ -40,9 +40,27 @@ struct TargetDesc {
   int64_t q_off;        // first query of this pair-realization in the debug predictions
   int64_t nbr_off;      // first entry in the debug neighbour lists
   int64_t lib_dbg_off;  // first entry in the debug libraries
+  int64_t obs_tile;     // observed-moment record of query tile 0 of (j, i, E, tau)
   int32_t i;            // target variable
   int32_t pad;
 };
+
+// Observed-moment job: one per (job, library variable j, target i, E, tau).
+// The observed values of a query tile (the target at the tile's manifold
+// points) do not depend on L or the realization, so their tile mean, centred
+// values and centred sum of squares are computed once per run and read by the
+// epilogue of every realization of that (j, i, E, tau).
+struct ObsJob {
+  int64_t series_off;   // element offset of the job's series block
+  int64_t n;            // series length
+  int64_t order_off;    // query order of (j, E, tau)
+  int64_t obs_tile;     // first tile record; the jobs' records are consecutive
+  int32_t i, E, tau, n_m, n_tiles;
+  int32_t pad;
+};
+// One tile record: x_q - mean(x) for the tile's 256 queries in query order
+// (zero past the tile's end), then mean(x) and sum of (x_q - mean(x))^2.
+constexpr int kObsStride = 264;        // doubles per record (64-byte multiple)
 
 // One work item of the fused kernel: a query tile of a unit.
 struct WorkItem {
@@ -97,6 +115,7 @@ struct KnnParams {
   const void* table;      // distance indexing tables (units with table_R > 0)
   int32_t table_u16;      // 1: uint16 entries (every manifold below 65536 points), 0: int32
   double* partials;       // 6 doubles per query tile
+  const double* obs;      // observed-moment tile records (TargetDesc::obs_tile)
   uint32_t* unit_done;    // per-unit tile counters (reset by the unit's last tile)
   uint32_t* item_counter; // dynamic scheduling counter (zeroed before each launch)
   double* rho;            // output (device), indexed by UnitDesc::out_idx
@@ -141,6 +160,10 @@ size_t knn_smem_bytes(int emin, int emax);
 cudaError_t knn_prepare();
 cudaError_t knn_occupancy(int E, int* ctas_per_sm);
 cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s);
+// Observed-moment records of every ObsJob (after the query order): one warp
+// per tile, n_tiles tiles in all.
+cudaError_t launch_obs(const float* series, const int32_t* order, const ObsJob* jobs,
+                       int64_t n_jobs, int64_t n_tiles, double* obs, cudaStream_t s);
 // Table path: same work items, neighbours read from the distance indexing table.
 size_t knn_table_smem(int max_nm);
 cudaError_t knn_table_prepare();

@@ -29,9 +29,10 @@
 //    during insertion keeps equal distances in index order;
 //  * the epilogue forms u_i = exp(-d_i/d_1) (optionally floored), the
 //    prediction, and the tile's FP64 moments (one warp does the FP64 work:
-//    the FP64 pipe is the scarce unit); the last tile of a realization to
-//    finish merges the tiles' moments in a fixed order, so rho does not
-//    depend on the schedule.
+//    the FP64 pipe is the scarce unit; the observed values' half of it is
+//    done once per (j, i, E, tau) by obs_kernel, not once per realization);
+//    the last tile of a realization to finish merges the tiles' moments in a
+//    fixed order, so rho does not depend on the schedule.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -177,53 +178,101 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Two-pass FP64 moments of one tile's (observed, predicted) pairs, staged in
-// shared memory (xs[0..nq), ys[0..nq)), by one warp: each lane sums a fixed
-// strided subset, then the butterfly.  Writes (n, mean_x, mean_y, Sxx, Syy,
-// Sxy) about the tile means.  One warp does the FP64 work that would
-// otherwise occupy all eight: the FP64 pipe is the scarce unit here.
-__device__ __forceinline__ void tile_moments(const double* xs, const double* ys, int nq,
+// Two-pass FP64 moments of one tile's (observed x, predicted y) pairs, by one
+// warp: each lane sums a fixed strided subset, then the butterfly.  The
+// predictions are staged in shared memory (ys[0..nq)); the observed half comes
+// from the tile's record (obs_kernel: x_q - mean(x), mean(x), Sxx), computed
+// there with the same lane order and butterfly.  Writes (n, mean_x, mean_y,
+// Sxx, Syy, Sxy) about the tile means.  One warp does the FP64 work that
+// would otherwise occupy all eight: the FP64 pipe is the scarce unit here.
+constexpr int kPer = kQT / 32;  // queries per lane
+
+// Mean of the nq lane-strided values v(c) = value lane + 32c (the sum in lane
+// order, then the butterfly); a full tile divides by 256 = 2^8, and
+// multiplying by 2^-8 gives the same bits and spares the FP64 pipe a division.
+template <class V>
+__device__ __forceinline__ double tile_mean(V v, int nq) {
+  const int lane = threadIdx.x & 31;
+  double sv = 0.0;
+#pragma unroll
+  for (int c = 0; c < kPer; ++c)
+    if (lane + 32 * c < nq) sv = __dadd_rn(sv, v(c));
+  sv = warp_sum(sv);
+  return (nq == kQT) ? __dmul_rn(sv, 1.0 / kQT) : __ddiv_rn(sv, (double)nq);
+}
+
+__device__ __forceinline__ void tile_moments(const double* ys, const double* rec, int nq,
                                              double* part) {
   const int lane = threadIdx.x & 31;
-  constexpr int kPer = kQT / 32;
-  double sx = 0.0, sy = 0.0;
+  const double my = tile_mean([&](int c) { return ys[lane + 32 * c]; }, nq);
+  double syy = 0.0, sxy = 0.0;
 #pragma unroll
   for (int c = 0; c < kPer; ++c) {
-    const int i = lane + 32 * c;
-    if (i < nq) {
-      sx = __dadd_rn(sx, xs[i]);
-      sy = __dadd_rn(sy, ys[i]);
-    }
-  }
-  sx = warp_sum(sx);
-  sy = warp_sum(sy);
-  const double n = (double)nq;
-  // a full tile divides by 256 = 2^8: multiplying by 2^-8 gives the same bits
-  // and spares the FP64 pipe two divisions
-  const bool full = nq == kQT;
-  const double mx = full ? __dmul_rn(sx, 1.0 / kQT) : __ddiv_rn(sx, n);
-  const double my = full ? __dmul_rn(sy, 1.0 / kQT) : __ddiv_rn(sy, n);
-  double sxx = 0.0, syy = 0.0, sxy = 0.0;
-#pragma unroll
-  for (int c = 0; c < kPer; ++c) {
-    const int i = lane + 32 * c;
-    if (i < nq) {  // second pass re-reads shared memory: registers are scarce here
-      const double a = __dsub_rn(xs[i], mx), b = __dsub_rn(ys[i], my);
-      sxx = __fma_rn(a, a, sxx);
+    const int q = lane + 32 * c;
+    if (q < nq) {  // the second pass re-reads shared memory: registers are scarce here
+      const double b = __dsub_rn(ys[q], my);
       syy = __fma_rn(b, b, syy);
-      sxy = __fma_rn(a, b, sxy);
+      sxy = __fma_rn(__ldg(rec + q), b, sxy);
     }
   }
-  sxx = warp_sum(sxx);
   syy = warp_sum(syy);
   sxy = warp_sum(sxy);
   if (lane == 0) {
-    part[0] = n;
-    part[1] = mx;
+    part[0] = (double)nq;
+    part[1] = __ldg(rec + kQT);
     part[2] = my;
-    part[3] = sxx;
+    part[3] = __ldg(rec + kQT + 1);
     part[4] = syy;
     part[5] = sxy;
+  }
+}
+
+// Observed-moment records (see ObsJob), one warp per tile: x_q is the target
+// at the tile's manifold points (Sect. 2.1: the value the cross map
+// predicts).  The same lane order and butterfly as tile_moments.
+__global__ void __launch_bounds__(kThreads) obs_kernel(const float* series, const int32_t* order,
+                                                      const ObsJob* jobs, int64_t n_jobs,
+                                                      int64_t n_tiles, double* obs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_tiles;
+       g += n_warps) {
+    int64_t lo = 0, hi = n_jobs - 1;  // the job holding tile g: last obs_tile <= g
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].obs_tile <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const ObsJob jb = jobs[lo];
+    const int tile = (int)(g - jb.obs_tile);
+    const int nq = min(kQT, jb.n_m - tile * kQT);
+    const float* si = series + jb.series_off + (int64_t)jb.i * jb.n;
+    const int32_t* ord = order + jb.order_off + (int64_t)tile * kQT;
+    const int off = (jb.E - 1) * jb.tau;
+    double x[kPer];
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+      const int q = lane + 32 * c;
+      x[c] = (q < nq) ? (double)si[ord[q] + off] : 0.0;
+    }
+    const double mx = tile_mean([&](int c) { return x[c]; }, nq);
+    double* rec = obs + g * kObsStride;
+    double sxx = 0.0;
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+      const int q = lane + 32 * c;
+      double a = 0.0;
+      if (q < nq) {
+        a = __dsub_rn(x[c], mx);
+        sxx = __fma_rn(a, a, sxx);
+      }
+      rec[q] = a;
+    }
+    sxx = warp_sum(sxx);
+    if (lane == 0) {
+      rec[kQT] = mx;
+      rec[kQT + 1] = sxx;
+    }
   }
 }
 
@@ -290,7 +339,7 @@ __device__ __noinline__ void complete_tile(const KnnParams& p, const UnitDesc& u
 // of every target, FP64 tile moments, and the merge of the moments by the
 // realization's last tile.
 //
-// `stage` is 4*kQT doubles of shared memory: two buffers, used alternately by
+// `stage` is 2*kQT doubles of shared memory: two buffers, used alternately by
 // successive stagings; k0 numbers this tile's first staging within the work
 // item (the same in every thread; a work item starts behind block barriers).
 // One warp per tile (rotating with the tile index) reduces the tile's moments,
@@ -341,12 +390,12 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
         for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nbc[s];
       }
     }
-    double* buf = stage + ((k0 + t) & 1) * 2 * kQT;
-    buf[tid] = valid ? (double)si[m + off] : 0.0;
-    buf[kQT + tid] = valid ? (double)xhat : 0.0;
+    double* buf = stage + ((k0 + t) & 1) * kQT;
+    buf[tid] = valid ? (double)xhat : 0.0;
     __syncthreads();
     if (warp == red)
-      tile_moments(buf, buf + kQT, nq, p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile));
+      tile_moments(buf, p.obs + (tg.obs_tile + tile) * kObsStride, nq,
+                   p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile));
   }
 
   if (warp == red) complete_tile(p, u, unit);
@@ -560,7 +609,7 @@ __device__ __forceinline__ float d2_point(const float* sj, int off, int tau, con
 // of every query (slot-major, one column per thread), then the library
 // membership map: one byte per manifold point when the manifold has at most
 // kByteMapMax points (a load and a compare per table entry), else one bit.
-constexpr int kStageBytes = 4 * kQT * 8;
+constexpr int kStageBytes = 2 * kQT * 8;
 constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
 constexpr int kByteMapMax = 32768;
 
@@ -779,6 +828,15 @@ cudaError_t launch_knn_table(const KnnParams& p, int E, int max_nm, int grid, cu
   return cudaErrorInvalidValue;
 }
 int knn_queries_per_thread() { return 1; }
+
+cudaError_t launch_obs(const float* series, const int32_t* order, const ObsJob* jobs,
+                       int64_t n_jobs, int64_t n_tiles, double* obs, cudaStream_t s) {
+  if (n_jobs <= 0 || n_tiles <= 0) return cudaSuccess;
+  const int64_t want = (n_tiles + kThreads / 32 - 1) / (kThreads / 32);  // a warp per tile
+  const int64_t blocks = want < 65536 ? want : 65536;
+  obs_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(series, order, jobs, n_jobs, n_tiles, obs);
+  return cudaGetLastError();
+}
 size_t knn_smem_bytes(int, int) { return kSmemBytes; }
 
 // One kernel per E (each keeps all its registers for that E's lists).

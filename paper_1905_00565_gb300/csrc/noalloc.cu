@@ -7,7 +7,8 @@
 // one (pair, E, tau, L) cell with r realizations from caller-owned device
 // input to caller-owned device output, and keeps every intermediate -- the
 // realization descriptors, the work items, the r libraries, the per-tile
-// partial moments and the counters -- in one file-scope device array of
+// partial moments, the observed-value tile records and the counters -- in one
+// file-scope device array of
 // kScratchBytes.  The array exists on every GPU that loads this library until
 // the process exits.
 //
@@ -30,14 +31,14 @@
 namespace ccm {
 
 // Scratch for one cell: descriptors, work items, libraries, partial moments,
-// counters, query order.  16 MiB holds, e.g., r = 250 realizations of L = 9000 at N = 10^4.
+// counters, query order, observed-value tile records.  16 MiB holds, e.g., r = 250 realizations of L = 9000 at N = 10^4.
 constexpr size_t kScratchBytes = 16u << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
 struct NoallocLayout {
-  size_t units, items, lib, part, done, err, counter, order, orderjob, target, total;
+  size_t units, items, lib, part, done, err, counter, order, orderjob, target, obs, obsjob, total;
 };
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
@@ -65,6 +66,10 @@ NoallocLayout noalloc_layout(int64_t r, int64_t L, int64_t n_tiles, int64_t n_m)
   o = up256(o + sizeof(OrderJob));
   a.target = o;
   o = up256(o + sizeof(TargetDesc) * (size_t)r);
+  a.obs = o;
+  o = up256(o + sizeof(double) * kObsStride * (size_t)n_tiles);
+  a.obsjob = o;
+  o = up256(o + sizeof(ObsJob));
   a.total = o;
   return a;
 }
@@ -115,6 +120,7 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     tg.q_off = k * (int64_t)c.n_m;
     tg.nbr_off = k * (int64_t)c.n_m * (c.E + 1);
     tg.lib_dbg_off = k * (int64_t)c.L;
+    tg.obs_tile = 0;
     tg.i = c.i;
     tg.pad = 0;
     reinterpret_cast<TargetDesc*>(scratch + lay.target)[k] = tg;
@@ -132,6 +138,18 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     oj.tau = c.tau;
     oj.n_m = c.n_m;
     *reinterpret_cast<OrderJob*>(scratch + lay.orderjob) = oj;
+    ObsJob ob;
+    ob.series_off = 0;
+    ob.n = c.n;
+    ob.order_off = 0;
+    ob.obs_tile = 0;
+    ob.i = c.i;
+    ob.E = c.E;
+    ob.tau = c.tau;
+    ob.n_m = c.n_m;
+    ob.n_tiles = c.n_tiles;
+    ob.pad = 0;
+    *reinterpret_cast<ObsJob*>(scratch + lay.obsjob) = ob;
     *reinterpret_cast<int32_t*>(scratch + lay.err) = 0;
     *reinterpret_cast<uint32_t*>(scratch + lay.counter) = 0u;
   }
@@ -204,6 +222,10 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   noalloc_setup_kernel<<<(unsigned)((r * n_tiles + 255) / 256), 256, 0, s>>>(scratch, lay, c);
   e = launch_order(d_series, reinterpret_cast<const OrderJob*>(scratch + lay.orderjob), 1,
                    (int)n_m, reinterpret_cast<int32_t*>(scratch + lay.order), nullptr, s);
+  if (e == cudaSuccess)
+    e = launch_obs(d_series, reinterpret_cast<const int32_t*>(scratch + lay.order),
+                   reinterpret_cast<const ObsJob*>(scratch + lay.obsjob), 1, n_tiles,
+                   reinterpret_cast<double*>(scratch + lay.obs), s);
   if (e != cudaSuccess) return noalloc_fail(CCM_ECUDA, cudaGetErrorString(e));
   SamplerParams sp{};
   sp.units = reinterpret_cast<const UnitDesc*>(scratch + lay.units);
@@ -222,6 +244,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   kp.lib = reinterpret_cast<const int32_t*>(scratch + lay.lib);
   kp.order = reinterpret_cast<const int32_t*>(scratch + lay.order);
   kp.partials = reinterpret_cast<double*>(scratch + lay.part);
+  kp.obs = reinterpret_cast<const double*>(scratch + lay.obs);
   kp.unit_done = reinterpret_cast<uint32_t*>(scratch + lay.done);
   kp.item_counter = reinterpret_cast<uint32_t*>(scratch + lay.counter);
   kp.rho = d_rho;

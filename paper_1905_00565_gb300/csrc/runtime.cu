@@ -143,6 +143,8 @@ struct UnitList {
   int64_t te_first[kMaxE + 1] = {};   // the same for the table items
   int64_t te_count[kMaxE + 1] = {};
   std::vector<OrderJob> orders;       // one per (job, library variable, E, tau)
+  std::vector<ObsJob> obs_jobs;       // one per (job, library variable, target, E, tau)
+  int64_t obs_total = 0;              // observed-moment tile records
   std::vector<TableJob> tables;       // distance indexing tables to build
   std::vector<WorkItem> items_table;  // work items of units that read a table
   std::vector<double> item_cost_table;
@@ -231,6 +233,30 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         }
         ul->orders.push_back(oj);
       }
+  // Observed-moment records per (j, i, E, tau), shared by every L and k.
+  std::map<std::tuple<int32_t, int32_t, int32_t, int32_t>, int64_t> obs_of;
+  for (int32_t j : lib_vars)
+    for (int64_t p : pairs_of[j])
+      for (int32_t E : pc.E)
+        for (int32_t tau : pc.tau) {
+          const int32_t i = pc.pairs[2 * p + 1];
+          const auto key = std::make_tuple(j, i, E, tau);
+          if (obs_of.count(key)) continue;
+          ObsJob ob;
+          std::memset(&ob, 0, sizeof(ob));
+          ob.series_off = series_off;
+          ob.n = pc.n;
+          ob.order_off = combo[std::make_tuple(j, E, tau)];
+          ob.obs_tile = ul->obs_total;
+          ob.i = i;
+          ob.E = E;
+          ob.tau = tau;
+          ob.n_m = (int32_t)(pc.n - (int64_t)(E - 1) * tau);
+          ob.n_tiles = (ob.n_m + tileq - 1) / tileq;
+          obs_of[key] = ob.obs_tile;
+          ul->obs_total += ob.n_tiles;
+          ul->obs_jobs.push_back(ob);
+        }
   // Distance indexing tables (unless CCM_NO_TABLE): per (j, E, tau),
   // realizations with L >= table_min_L read their neighbours from a table of
   // the R nearest points of every query; R covers about four times the
@@ -322,6 +348,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
               tg.nbr_off = nbr_off[(size_t)o];
               tg.lib_dbg_off = lib_off[(size_t)o];
               tg.i = pc.pairs[2 * p + 1];
+              tg.obs_tile = obs_of[std::make_tuple(j, tg.i, E, tau)];
               ul->targets.push_back(tg);
             }
             const auto tab = table_of.find(std::make_tuple(j, E, tau));
@@ -427,7 +454,7 @@ void sort_items(UnitList* ul) {
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
          counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
-         items_table = 0, order_scratch = 0, total = 0;
+         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, total = 0;
 };
 
 Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
@@ -455,6 +482,8 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.table = take(ul.table_elem() * (size_t)ul.table_total);
   a.tables = take(sizeof(TableJob) * ul.tables.size());
   a.items_table = take(sizeof(WorkItem) * ul.items_table.size());
+  a.obs = take(sizeof(double) * kObsStride * (size_t)ul.obs_total);
+  a.obs_jobs = take(sizeof(ObsJob) * ul.obs_jobs.size());
   a.total = o;
   return a;
 }
@@ -612,6 +641,7 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.table = base + ar.table;
   kp.table_u16 = ul.table_u16();
   kp.partials = reinterpret_cast<double*>(base + ar.part);
+  kp.obs = reinterpret_cast<const double*>(base + ar.obs);
   kp.unit_done = reinterpret_cast<uint32_t*>(base + ar.done);
   kp.item_counter = reinterpret_cast<uint32_t*>(base + ar.counter);
   kp.rho = reinterpret_cast<double*>(base + ar.rho);
@@ -624,8 +654,16 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   return kp;
 }
 
+cudaError_t enqueue_obs(char* base, const Arena& ar, const UnitList& ul, cudaStream_t s) {
+  return launch_obs(reinterpret_cast<const float*>(base + ar.series),
+                    reinterpret_cast<const int32_t*>(base + ar.order),
+                    reinterpret_cast<const ObsJob*>(base + ar.obs_jobs),
+                    (int64_t)ul.obs_jobs.size(), ul.obs_total,
+                    reinterpret_cast<double*>(base + ar.obs), s);
+}
+
 // Enqueue sampler + fused kernel for a whole unit list on stream s.
-// Stage events (optional): ev[0] start, ev[1] after order + table build,
+// Stage events (optional): ev[0] start, ev[1] after order, observed moments and table build,
 // ev[2] after the sampler, ev[3] after the brute-force launch, ev[4] after the
 // table-scan launch.
 ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const Tuning& tn,
@@ -647,6 +685,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                         (int64_t)ul.orders.size(), ul.max_nm,
                         reinterpret_cast<int32_t*>(base + ar.order),
                         reinterpret_cast<unsigned long long*>(base + ar.order_scratch), s));
+  CCM_CUDA(enqueue_obs(base, ar, ul, s));
   CCM_CUDA(launch_table_build(reinterpret_cast<const float*>(base + ar.series),
                               reinterpret_cast<const TableJob*>(base + ar.tables),
                               (int64_t)ul.tables.size(), ul.max_nm, ul.max_R,
@@ -769,6 +808,7 @@ ccm_status autotune(ccm_plan_s* pl, cudaStream_t s) {
                         (int64_t)ul.orders.size(), ul.max_nm,
                         reinterpret_cast<int32_t*>(base + ar.order),
                         reinterpret_cast<unsigned long long*>(base + ar.order_scratch), s));
+  CCM_CUDA(enqueue_obs(base, ar, ul, s));
   SamplerParams sp = sampler_params(base, ar);
   CCM_CUDA(launch_sampler(sp, 0, (int64_t)ul.units.size(), ul.max_nm, s));
   const int want = 6 * ctx->sm_count;
@@ -907,6 +947,9 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
     e = cudaMemcpy(pl->d_arena + pl->ar.tables, pl->ul.tables.data(),
                    sizeof(TableJob) * pl->ul.tables.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_arena + pl->ar.obs_jobs, pl->ul.obs_jobs.data(),
+                   sizeof(ObsJob) * pl->ul.obs_jobs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_arena + pl->ar.items_table, pl->ul.items_table.data(),
                    sizeof(WorkItem) * pl->ul.items_table.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
@@ -940,7 +983,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.table_bytes = pl->ul.table_elem() * (size_t)pl->ul.table_total;
   // launches of one ccm_run: order, tables, sampler, one brute-force and one
   // table-scan kernel per E present
-  in.launches_per_run = 2 + (pl->ul.tables.empty() ? 0 : 1);
+  in.launches_per_run = 3 + (pl->ul.tables.empty() ? 0 : 1);  // order, observed moments, sampler
   for (int E = 1; E <= kMaxE; ++E)
     in.launches_per_run += (pl->ul.e_count[E] > 0 ? 1 : 0) + (pl->ul.te_count[E] > 0 ? 1 : 0);
   *out = pl.release();
@@ -1231,23 +1274,27 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
   }
   // Descriptors go through pinned staging: a copy from pageable memory would
   // wait for earlier work on this (reused) stream.
-  // (units, work items, order jobs, targets, table jobs, table work items)
-  const void* src[6] = {b->ul.units.data(), b->ul.items.data(), b->ul.orders.data(),
-                        b->ul.targets.data(), b->ul.tables.data(), b->ul.items_table.data()};
-  const size_t len[6] = {sizeof(UnitDesc) * b->ul.units.size(),
-                         sizeof(WorkItem) * b->ul.items.size(),
-                         sizeof(OrderJob) * b->ul.orders.size(),
-                         sizeof(TargetDesc) * b->ul.targets.size(),
-                         sizeof(TableJob) * b->ul.tables.size(),
-                         sizeof(WorkItem) * b->ul.items_table.size()};
-  const size_t dst[6] = {b->ar.units, b->ar.items, b->ar.orders, b->ar.targets, b->ar.tables,
-                         b->ar.items_table};
+  // (units, work items, order jobs, targets, table jobs, table work items,
+  // observed-moment jobs)
+  constexpr int kMeta = 7;
+  const void* src[kMeta] = {b->ul.units.data(),   b->ul.items.data(),  b->ul.orders.data(),
+                            b->ul.targets.data(), b->ul.tables.data(), b->ul.items_table.data(),
+                            b->ul.obs_jobs.data()};
+  const size_t len[kMeta] = {sizeof(UnitDesc) * b->ul.units.size(),
+                             sizeof(WorkItem) * b->ul.items.size(),
+                             sizeof(OrderJob) * b->ul.orders.size(),
+                             sizeof(TargetDesc) * b->ul.targets.size(),
+                             sizeof(TableJob) * b->ul.tables.size(),
+                             sizeof(WorkItem) * b->ul.items_table.size(),
+                             sizeof(ObsJob) * b->ul.obs_jobs.size()};
+  const size_t dst[kMeta] = {b->ar.units,  b->ar.items,       b->ar.orders,  b->ar.targets,
+                             b->ar.tables, b->ar.items_table, b->ar.obs_jobs};
   b->meta_bytes = 0;
-  for (int q = 0; q < 6; ++q) b->meta_bytes += len[q];
+  for (int q = 0; q < kMeta; ++q) b->meta_bytes += len[q];
   b->h_meta = pinned_get(ctx, b->meta_bytes);
   if (!b->h_meta) return fail(CCM_ENOMEM, "pinned allocation failed");
   char* hm = static_cast<char*>(b->h_meta);
-  for (int q = 0; q < 6; ++q) {
+  for (int q = 0; q < kMeta; ++q) {
     if (len[q] == 0) continue;
     std::memcpy(hm, src[q], len[q]);
     CCM_CUDA(cudaMemcpyAsync(base + dst[q], hm, len[q], cudaMemcpyHostToDevice, b->stream));
