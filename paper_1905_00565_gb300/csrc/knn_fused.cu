@@ -48,11 +48,15 @@ constexpr int kThreads = 256;             // threads per CTA = queries per tile
 constexpr int kQT = kThreads;             // queries per tile (one per thread)
 static_assert((kQT & (kQT - 1)) == 0, "tile moments rely on a power-of-two tile");
 constexpr int kBuf = 16;                  // pending candidates per query
-constexpr int kCoordBytes = 40 * 1024;    // shared memory for one library tile + chunk boxes
+constexpr int kCoordBytes = 32 * 1024;    // shared memory for one library tile + chunk boxes
 constexpr int kBoxBytes = 2 * 1024;       // chunk bounding boxes, at the end of that region
 constexpr int kChunk = 32;                // library points per bounding box
 constexpr int kBufBytes = kBuf * kThreads * 8;
-constexpr int kSmemBytes = kCoordBytes + kBufBytes;
+// Predictions staged for their FP64 moments: kRing (tile, target) vectors of
+// kQT floats, reduced together, one warp each, when the ring is full.
+constexpr int kRing = kThreads / 32;
+constexpr int kRingBytes = kRing * kThreads * 4;
+constexpr int kSmemBytes = kCoordBytes + kBufBytes + kRingBytes;
 constexpr unsigned kFull = 0xffffffffu;
 // Kernel variants picked per E by the autotuner (results are identical):
 //   V = 0 "narrow": 4 library points per step, no early termination;
@@ -183,8 +187,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // predictions are staged in shared memory (ys[0..nq)); the observed half comes
 // from the tile's record (obs_kernel: x_q - mean(x), mean(x), Sxx), computed
 // there with the same lane order and butterfly.  Writes (n, mean_x, mean_y,
-// Sxx, Syy, Sxy) about the tile means.  One warp does the FP64 work that
-// would otherwise occupy all eight: the FP64 pipe is the scarce unit here.
+// Sxx, Syy, Sxy) about the tile means.
 constexpr int kPer = kQT / 32;  // queries per lane
 
 // Mean of the nq lane-strided values v(c) = value lane + 32c (the sum in lane
@@ -201,16 +204,19 @@ __device__ __forceinline__ double tile_mean(V v, int nq) {
   return (nq == kQT) ? __dmul_rn(sv, 1.0 / kQT) : __ddiv_rn(sv, (double)nq);
 }
 
-__device__ __forceinline__ void tile_moments(const double* ys, const double* rec, int nq,
+__device__ __forceinline__ void tile_moments(const float* ys, const double* rec, int nq,
                                              double* part) {
   const int lane = threadIdx.x & 31;
-  const double my = tile_mean([&](int c) { return ys[lane + 32 * c]; }, nq);
+  double y[kPer];
+#pragma unroll
+  for (int c = 0; c < kPer; ++c) y[c] = (double)ys[lane + 32 * c];
+  const double my = tile_mean([&](int c) { return y[c]; }, nq);
   double syy = 0.0, sxy = 0.0;
 #pragma unroll
   for (int c = 0; c < kPer; ++c) {
     const int q = lane + 32 * c;
-    if (q < nq) {  // the second pass re-reads shared memory: registers are scarce here
-      const double b = __dsub_rn(ys[q], my);
+    if (q < nq) {
+      const double b = __dsub_rn(y[c], my);
       syy = __fma_rn(b, b, syy);
       sxy = __fma_rn(__ldg(rec + q), b, sxy);
     }
@@ -311,11 +317,12 @@ __device__ __forceinline__ double merge_moments(const double* base, int n_tiles)
   return (SXX > 0.0 && SYY > 0.0) ? __ddiv_rn(SXY, __dsqrt_rn(__dmul_rn(SXX, SYY))) : nan("");
 }
 
-// Called by a tile's reducer warp after its lane 0 wrote every target's
-// moments of the tile: the fence orders them before the completion count, and
-// the last tile of the realization to arrive merges them all.  Out of line:
-// it runs once per tile, and inlined its registers would crowd the search.
-__device__ __noinline__ void complete_tile(const KnnParams& p, const UnitDesc& u, int unit) {
+// Called by a reducer warp after its lane 0 wrote the moments of one (tile,
+// target) of a realization: the fence orders them before the completion
+// count, and the last of the realization's n_tiles * n_targets to arrive
+// merges every target's moments.  Out of line: inlined its registers would
+// crowd the search.
+__device__ __noinline__ void complete_tile(const KnnParams& p, int unit) {
   const int lane = threadIdx.x & 31;
   unsigned prev = 0u;
   if (lane == 0) {
@@ -323,37 +330,61 @@ __device__ __noinline__ void complete_tile(const KnnParams& p, const UnitDesc& u
     prev = atomicAdd(&p.unit_done[unit], 1u);
   }
   prev = __shfl_sync(kFull, prev, 0);
-  if (prev != (unsigned)(u.n_tiles - 1)) return;
+  const UnitDesc& u = p.units[unit];
+  const int n_tiles = u.n_tiles, n_targets = u.n_targets;
+  if (prev != (unsigned)(n_tiles * n_targets - 1)) return;
   __threadfence();
-  for (int t = 0; t < u.n_targets; ++t) {
-    const double r = merge_moments(p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles),
-                                   u.n_tiles);
+  for (int t = 0; t < n_targets; ++t) {
+    const double r = merge_moments(p.partials + 6 * (u.part_off + (int64_t)t * n_tiles), n_tiles);
     if (lane == 0) p.rho[p.targets[u.tgt_off + t].out_idx] = r;
   }
   if (lane == 0) p.unit_done[unit] = 0u;  // ready for the next run
 }
 
+// A staged (tile, target) prediction vector awaiting its FP64 moments.
+struct RingMeta {
+  const double* rec;  // the tile's observed-value record
+  double* part;       // where its six moments go
+  int32_t unit;       // its realization
+  int32_t nq;         // valid queries of the tile
+};
+
+// The staged vectors' moments: warps 0..n-1 take one each, in parallel (so the
+// FP64 pipes of all four SM sub-partitions share the work), and count it
+// towards its realization's completion.  Between two block barriers: the
+// slots are complete on entry and free again on exit.
+__device__ __forceinline__ void flush_ring(const KnnParams& p, const float* ring,
+                                           const RingMeta* meta, int n) {
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp < n) {
+    const RingMeta mt = meta[warp];
+    tile_moments(ring + warp * kQT, mt.rec, mt.nq, mt.part);
+    complete_tile(p, mt.unit);
+  }
+  __syncthreads();
+}
+
 // Everything after the neighbour search, shared by the brute-force and the
 // table paths: dd[0..E] ascending FP32 squared distances and nb[0..E] the
-// neighbours of query m (itself excluded).  Simplex weights, the prediction
-// of every target, FP64 tile moments, and the merge of the moments by the
-// realization's last tile.
-//
-// `stage` is 2*kQT doubles of shared memory: two buffers, used alternately by
-// successive stagings; k0 numbers this tile's first staging within the work
-// item (the same in every thread; a work item starts behind block barriers).
-// One warp per tile (rotating with the tile index) reduces the tile's moments,
-// signals completion and, for the realization's last tile, merges; the other
-// warps go on.  Staging k writes its buffer after the barrier of staging k-1,
-// which the reducer of staging k-2 reaches only after it has finished with
-// that buffer.  kBarriers (brute-force path): the stage buffers overlap memory
-// the search still reads, so every thread arrives first; and one more barrier
-// at the end, which also keeps the search's registers free of spills.
-template <int E, bool kBarriers>
+// neighbours of query m (itself excluded).  Simplex weights and the
+// prediction of every target; each target's prediction vector goes to the
+// next ring slot (ring_n, the same in every thread), and a full ring is
+// reduced (flush_ring).  The CTA flushes what is left when it runs out of
+// work.  rho does not depend on which warp reduced which vector, or when.
+// `keep` (brute-force path: the thread's own column of the candidate buffer,
+// which only this thread uses and which is free once its search is done)
+// holds the weights and neighbours in shared memory, so that a reduction
+// between two targets finds no live registers to spill; other warps may still
+// be searching, so nothing else of the buffer is touched.  kKeep false: they
+// stay in registers.
+static_assert(kMaxE + 1 <= kBuf, "the epilogue keeps E+1 entries in a candidate column");
+template <int E, bool kKeep>
 __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& u, int unit,
                                             int tile, int m, bool valid, const float (&dd)[E + 1],
-                                            const int (&nb)[E + 1], double* stage, int k0) {
-  const int tid = threadIdx.x, warp = tid >> 5;
+                                            const int (&nb)[E + 1], float* ring, RingMeta* meta,
+                                            int& ring_n, u64* keep) {
+  const int tid = threadIdx.x;
   const int n_m = u.n_m;
   const int off = (E - 1) * u.tau;
   const int nq = min(kQT, n_m - tile * kQT);  // valid queries of this tile (>= 1)
@@ -372,39 +403,46 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
     // an unfilled slot (only possible with non-finite device input) reads, and
     // is reported, in bounds
     nbc[s] = min(max(nb[s], 0), n_m - 1);
+    if (kKeep) keep[s * kThreads + tid] = ((u64)__float_as_uint(w[s]) << 32) | (uint32_t)nbc[s];
   }
-  if (kBarriers) __syncthreads();  // every thread is done with the search's shared memory
-  const int red = tile & (kThreads / 32 - 1);  // this tile's reducer warp
-
+  auto weight = [&](int s) {
+    return kKeep ? __uint_as_float((uint32_t)(keep[s * kThreads + tid] >> 32)) : w[s];
+  };
+  auto nbr = [&](int s) { return kKeep ? (int)(uint32_t)keep[s * kThreads + tid] : nbc[s]; };
   for (int t = 0; t < u.n_targets; ++t) {
     const TargetDesc tg = p.targets[u.tgt_off + t];
     const float* si = p.series + u.series_off + (int64_t)tg.i * u.n;
     float acc = 0.f;
 #pragma unroll
-    for (int s = 0; s <= E; ++s) acc = __fmaf_rn(w[s], si[nbc[s] + off], acc);
+    for (int s = 0; s <= E; ++s) acc = __fmaf_rn(weight(s), si[nbr(s) + off], acc);
     const float xhat = __fdiv_rn(acc, usum);
     if (valid) {
       if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
       if (p.dbg_nbr) {
 #pragma unroll
-        for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nbc[s];
+        for (int s = 0; s <= E; ++s) p.dbg_nbr[tg.nbr_off + (int64_t)m * (E + 1) + s] = nbr(s);
       }
     }
-    double* buf = stage + ((k0 + t) & 1) * kQT;
-    buf[tid] = valid ? (double)xhat : 0.0;
-    __syncthreads();
-    if (warp == red)
-      tile_moments(buf, p.obs + (tg.obs_tile + tile) * kObsStride, nq,
-                   p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile));
+    ring[ring_n * kQT + tid] = valid ? xhat : 0.f;
+    if (tid == 0)
+      meta[ring_n] = RingMeta{p.obs + (tg.obs_tile + tile) * kObsStride,
+                              p.partials + 6 * (u.part_off + (int64_t)t * u.n_tiles + tile), unit,
+                              nq};
+    // a full ring is reduced before the next target's vector, or at the end
+    if (++ring_n == kRing && t + 1 < u.n_targets) {
+      flush_ring(p, ring, meta, kRing);
+      ring_n = 0;
+    }
   }
-
-  if (warp == red) complete_tile(p, u, unit);
-  if (kBarriers) __syncthreads();
+  if (ring_n == kRing) {  // the weights and neighbours are dead here
+    flush_ring(p, ring, meta, kRing);
+    ring_n = 0;
+  }
 }
 
 template <int E, int V>
 __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, int tile,
-                             unsigned char* smem) {
+                             unsigned char* smem, RingMeta* meta, int& ring_n) {
   constexpr int K = E + 1;  // the window keeps m itself out, so E+1 slots suffice
   constexpr int EP = TileShape<E>::EP;
   constexpr int LT = TileShape<E>::LT;
@@ -413,6 +451,7 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   int32_t* s_lidx = reinterpret_cast<int32_t*>(smem + (size_t)(LT / 2) * EP * 8);  // [LT]
   float* s_box = reinterpret_cast<float*>(smem + kCoordBytes - kBoxBytes);       // [LT/32][2D]
   u64* s_buf = reinterpret_cast<u64*>(smem + kCoordBytes);                      // [kBuf][kThreads]
+  float* s_ring = reinterpret_cast<float*>(smem + kCoordBytes + kBufBytes);      // [kRing][kQT]
 
   const int tid = threadIdx.x, lane = tid & 31;
   const int n_m = u.n_m, L = u.L, tau = u.tau, W = u.theiler;
@@ -581,8 +620,11 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
     dd[s] = key_dist(ku[s]);
     nb[s] = key_index(ku[s]);
   }
-  // the library tile in shared memory is free once every thread is in the epilogue
-  finish_tile<E, true>(p, u, unit, tile, m, valid, dd, nb, reinterpret_cast<double*>(smem), 0);
+  finish_tile<E, true>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n,
+                       s_buf);
+  // the next tile's search starts behind a barrier (this also keeps the
+  // search's registers free of spills)
+  __syncthreads();
 }
 
 // --------------------------------------------------------------------------
@@ -605,25 +647,24 @@ __device__ __forceinline__ float d2_point(const float* sj, int off, int tau, con
   return acc;
 }
 
-// Shared memory of the table kernel: the epilogue's staging buffer, the hits
+// Shared memory of the table kernel: the epilogue's ring of predictions, the hits
 // of every query (slot-major, one column per thread), then the library
 // membership map: one byte per manifold point when the manifold has at most
 // kByteMapMax points (a load and a compare per table entry), else one bit.
-constexpr int kStageBytes = 2 * kQT * 8;
 constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
 constexpr int kByteMapMax = 32768;
 
 template <int E>
 __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
-                                   unsigned char* smem) {
+                                   unsigned char* smem, RingMeta* meta, int& ring_n) {
   const int tid = threadIdx.x;
   const int n_m = u.n_m, L = u.L, tau = u.tau, R = u.table_R, W = u.theiler;
   const int off = (E - 1) * tau;
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
   const int32_t* lib = p.lib + u.lib_off;
-  double* stage = reinterpret_cast<double*>(smem);
-  int32_t* s_hit = reinterpret_cast<int32_t*>(smem + kStageBytes);
-  unsigned char* map = smem + kStageBytes + kHitBytes;
+  float* s_ring = reinterpret_cast<float*>(smem);
+  int32_t* s_hit = reinterpret_cast<int32_t*>(smem + kRingBytes);
+  unsigned char* map = smem + kRingBytes + kHitBytes;
   const bool bytes = n_m <= kByteMapMax;
   const int words = bytes ? (n_m + 3) >> 2 : (n_m + 31) >> 5;  // 32-bit words of the map
   uint32_t* mw = reinterpret_cast<uint32_t*>(map);
@@ -731,8 +772,7 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
 #pragma unroll
     for (int s2 = 0; s2 <= E; ++s2)
       dd[s2] = valid ? d2_point<E>(sj, off, tau, q, max(nb[s2], 0)) : 0.f;
-    finish_tile<E, false>(p, u, unit, tile, m, valid, dd, nb, stage,
-                          (tile - tile0) * u.n_targets);
+    finish_tile<E, false>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr);
   }
 }
 
@@ -740,6 +780,8 @@ template <int E>
 __global__ void __launch_bounds__(kThreads, 3) knn_table_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
+  __shared__ RingMeta s_meta[kRing];
+  int ring_n = 0;  // staged prediction vectors (the same in every thread)
   for (int64_t round = 0;; ++round) {
     if (p.persistent) {
       if (threadIdx.x == 0) s_item = (int)atomicAdd(p.item_counter, 1u);
@@ -754,14 +796,17 @@ __global__ void __launch_bounds__(kThreads, 3) knn_table_kernel(KnnParams p) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
       continue;
     }
-    process_table_item<E>(p, u, w.unit, w.tile, smem);
+    process_table_item<E>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
   }
+  if (ring_n > 0) flush_ring(p, reinterpret_cast<const float*>(smem), s_meta, ring_n);
 }
 
 template <int E>
 __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
+  __shared__ RingMeta s_meta[kRing];
+  int ring_n = 0;  // staged prediction vectors (the same in every thread)
   for (int64_t round = 0;; ++round) {
     if (p.persistent) {
       if (threadIdx.x == 0) s_item = (int)atomicAdd(p.item_counter, 1u);
@@ -777,10 +822,12 @@ __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
       continue;
     }
     if (p.variant[E] == 1)
-      process_tile<E, 1>(p, u, w.unit, w.tile, smem);
+      process_tile<E, 1>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
     else
-      process_tile<E, 0>(p, u, w.unit, w.tile, smem);
+      process_tile<E, 0>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
   }
+  if (ring_n > 0)
+    flush_ring(p, reinterpret_cast<const float*>(smem + kCoordBytes + kBufBytes), s_meta, ring_n);
 }
 
 }  // namespace
@@ -792,7 +839,7 @@ size_t knn_table_smem(int max_nm) {
   const size_t bits = (size_t)((max_nm + 31) / 32) * 4;
   const size_t map = (max_nm <= kByteMapMax) ? (size_t)(max_nm + 3) / 4 * 4
                                              : (bits > (size_t)kByteMapMax ? bits : kByteMapMax);
-  return (size_t)kStageBytes + kHitBytes + map + 16;
+  return (size_t)kRingBytes + kHitBytes + map + 16;
 }
 
 #define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
