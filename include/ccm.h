@@ -12,8 +12,10 @@
  *       (Sect. 1: lagged embedding; Sect. 3.2: "lagged-coordinate vector");
  *     - a random library of L distinct manifold points (Sect. 1: r random
  *       subsamples of size L; Sect. 3.1).  Point m is chosen when its key
- *       ((hi32(Philox4x64-10(ctr=(m, k, L, (j<<16)|(E<<8)|tau),
- *       key=(seed, 0)).word0)) << 32 | m) is among the L smallest;
+ *       (v << 32 | m) is among the L smallest, v being 32-bit half number
+ *       m mod 8 (hi(w0), lo(w0), hi(w1), ..., lo(w3)) of the block
+ *       Philox4x64-10(ctr=(floor(m/8), k, L, (j<<16)|(E<<8)|tau),
+ *       key=(seed, 0));
  *     - for every manifold point m (all N_m points are queries) its E+1
  *       nearest library points, m itself excluded (optionally every l with
  *       |l - m| <= W, ccm_problem.theiler), ordered by (squared FP32

@@ -88,22 +88,26 @@ void philox4x64_10(const uint64_t in_ctr[4], const uint64_t in_key[2], uint64_t 
 
 // ---------------------------------------------------------------------------
 // Library sampling without replacement (Sect. 1: r random subsamples of size
-// L; Sect. 3.1).  Random-key selection: manifold point m gets the key whose
-// high 32 bits are the high 32 bits of Philox word 0 at counter
-// (m, k, L, (j<<16)|(E<<8)|tau) under key (seed, 0), and whose low 32 bits are
-// m.  The L points with the smallest keys form the library, listed in
-// ascending m.  Keys are distinct (m is in them), so the choice has no ties.
+// L; Sect. 3.1; the paper names no generator).  Random-key selection:
+// manifold point m gets the key whose high 32 bits are 32-bit half number
+// m mod 8 of the Philox block at counter (floor(m/8), k, L,
+// (j<<16)|(E<<8)|tau) under key (seed, 0) -- the halves taken in the order
+// high(w0), low(w0), high(w1), ..., low(w3) -- and whose low 32 bits are m.
+// The L points with the smallest keys form the library, listed in ascending
+// m.  Keys are distinct (m is in them), so the choice has no ties.
 // ---------------------------------------------------------------------------
 void sample_library(int64_t n_m, int64_t L, int32_t j, int32_t E, int32_t tau, int32_t k,
                     uint64_t seed, int32_t* lib) {
   std::vector<uint64_t> keys((size_t)n_m);
   const uint64_t key[2] = {seed, 0};
   for (int64_t m = 0; m < n_m; ++m) {
-    const uint64_t ctr[4] = {(uint64_t)m, (uint64_t)k, (uint64_t)L,
+    const uint64_t ctr[4] = {(uint64_t)(m / 8), (uint64_t)k, (uint64_t)L,
                              ((uint64_t)j << 16) | ((uint64_t)E << 8) | (uint64_t)tau};
     uint64_t w[4];
     philox4x64_10(ctr, key, w);
-    keys[(size_t)m] = ((w[0] >> 32) << 32) | (uint64_t)m;
+    const uint64_t word = w[(m % 8) / 2];
+    const uint64_t half = (m % 2 == 0) ? (word >> 32) : (word & 0xFFFFFFFFULL);
+    keys[(size_t)m] = (half << 32) | (uint64_t)m;
   }
   std::sort(keys.begin(), keys.end());
   std::vector<int32_t> chosen((size_t)L);

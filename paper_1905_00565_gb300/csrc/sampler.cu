@@ -3,10 +3,12 @@
 // pipeline input is a set of subsamples per (tau, E, L)).
 //
 // Random-key selection: manifold point m of unit (j, E, tau, L, k) gets the
-// 64-bit key (hi32(w0) << 32) | m, where w0 is word 0 of Philox4x64-10 at
-// counter (m, k, L, (j<<16)|(E<<8)|tau) under key (seed, 0).  The library is
-// the L points with the smallest keys, written in ascending m.  Keys are
-// distinct, so the selection is a pure function of the counter.
+// 64-bit key (v << 32) | m, where v is 32-bit half number m mod 8 of the
+// Philox4x64-10 block at counter (floor(m/8), k, L, (j<<16)|(E<<8)|tau) under
+// key (seed, 0), the halves numbered hi(w0), lo(w0), hi(w1), ..., lo(w3): one
+// block gives the keys of eight consecutive points.  The library is the L
+// points with the smallest keys, written in ascending m.  Keys are distinct,
+// so the selection is a pure function of the counter.
 //
 // One CTA per unit.  The high halves h(m) are computed once into shared memory
 // (or recomputed per pass when N_m is too large), an 8-bit radix select over
@@ -22,9 +24,10 @@ namespace ccm {
 namespace {
 
 // Philox4x64-10 (Salmon et al., SC'11): ten rounds, two 64x64->128 products per
-// round, round keys bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint64_t philox_word0(uint64_t c0, uint64_t c1, uint64_t c2,
-                                                 uint64_t c3, uint64_t k0, uint64_t k1) {
+// round, round keys bumped by the Weyl constants between rounds.  Writes the
+// four output words.
+__device__ __forceinline__ void philox_block(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                             uint64_t k0, uint64_t k1, uint64_t (&w)[4]) {
   const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
   const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
 #pragma unroll
@@ -41,12 +44,30 @@ __device__ __forceinline__ uint64_t philox_word0(uint64_t c0, uint64_t c1, uint6
     c2 = n2;
     c3 = lo0;
   }
-  return c0;
+  w[0] = c0;
+  w[1] = c1;
+  w[2] = c2;
+  w[3] = c3;
 }
 
-__device__ __forceinline__ uint32_t key_hi(const UnitDesc& u, int m) {
+// The Philox block holding the keys of points 8b .. 8b+7.
+__device__ __forceinline__ void key_block(const UnitDesc& u, int b, uint64_t (&w)[4]) {
   const uint64_t c3 = ((uint64_t)u.j << 16) | ((uint64_t)u.E << 8) | (uint64_t)u.tau;
-  return (uint32_t)(philox_word0((uint64_t)m, (uint64_t)u.k, (uint64_t)u.L, c3, u.seed, 0) >> 32);
+  philox_block((uint64_t)b, (uint64_t)u.k, (uint64_t)u.L, c3, u.seed, 0, w);
+}
+
+// 32-bit half number i (0..7) of a block: hi(w0), lo(w0), hi(w1), ..., lo(w3).
+__device__ __forceinline__ uint32_t block_half(const uint64_t (&w)[4], int i) {
+  const int q = i >> 1;
+  const uint64_t x = (q == 0) ? w[0] : (q == 1) ? w[1] : (q == 2) ? w[2] : w[3];
+  return (i & 1) ? (uint32_t)x : (uint32_t)(x >> 32);
+}
+
+// The high half of point m's key (one block per call).
+__device__ __forceinline__ uint32_t key_hi(const UnitDesc& u, int m) {
+  uint64_t w[4];
+  key_block(u, m >> 3, w);
+  return block_half(w, m & 7);
 }
 
 // Stable compaction of the members among positions [0, n) by the whole block,
@@ -87,7 +108,7 @@ __device__ uint32_t block_compact(int n, Item item, Member is_member, int32_t* o
 template <bool kInSmem>
 __global__ void __launch_bounds__(kSamplerThreads)
 sampler_kernel(SamplerParams p, int64_t first_unit) {
-  extern __shared__ uint32_t s_keys[];
+  extern __shared__ __align__(16) uint32_t s_keys[];
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_prefix, s_rank, s_neq;
@@ -101,8 +122,15 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
     if (threadIdx.x == 0) atomicOr(p.err, kErrSampler);
     return;
   }
-  if (kInSmem) {
-    for (int m = threadIdx.x; m < n_m; m += blockDim.x) s_keys[m] = key_hi(u, m);
+  const int n_blocks = (n_m + 7) >> 3;
+  if (kInSmem) {  // the key array is padded to whole blocks of eight
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) {
+      uint64_t w[4];
+      key_block(u, b, w);
+      uint4* dst = reinterpret_cast<uint4*>(s_keys + 8 * b);
+      dst[0] = make_uint4(block_half(w, 0), block_half(w, 1), block_half(w, 2), block_half(w, 3));
+      dst[1] = make_uint4(block_half(w, 4), block_half(w, 5), block_half(w, 6), block_half(w, 7));
+    }
   }
   if (threadIdx.x == 0) {
     s_prefix = 0u;
@@ -114,9 +142,21 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
     for (int b = threadIdx.x; b < 256; b += blockDim.x) s_hist[b] = 0u;
     __syncthreads();
     const uint32_t prefix = s_prefix;
-    for (int m = threadIdx.x; m < n_m; m += blockDim.x) {
-      const uint32_t h = kInSmem ? s_keys[m] : key_hi(u, m);
-      if ((h & mask) == prefix) atomicAdd(&s_hist[(h >> shift) & 255u], 1u);
+    if (kInSmem) {
+      for (int m = threadIdx.x; m < n_m; m += blockDim.x) {
+        const uint32_t h = s_keys[m];
+        if ((h & mask) == prefix) atomicAdd(&s_hist[(h >> shift) & 255u], 1u);
+      }
+    } else {  // recomputed, a block of eight keys per call
+      for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) {
+        uint64_t w[4];
+        key_block(u, b, w);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t h = block_half(w, i);
+          if (8 * b + i < n_m && (h & mask) == prefix) atomicAdd(&s_hist[(h >> shift) & 255u], 1u);
+        }
+      }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -206,7 +246,7 @@ cudaError_t launch_sampler(const SamplerParams& p, int64_t first_unit, int64_t c
                            cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (max_nm <= kSamplerSmemKeys) {
-    const size_t smem = (size_t)max_nm * sizeof(uint32_t);
+    const size_t smem = (size_t)((max_nm + 7) / 8 * 8) * sizeof(uint32_t);  // whole blocks
     for (int64_t off = 0; off < count; off += 0x7fffffff) {
       const unsigned grid = (unsigned)((count - off) < 0x7fffffff ? (count - off) : 0x7fffffff);
       sampler_kernel<true><<<grid, kSamplerThreads, smem, s>>>(p, first_unit + off);

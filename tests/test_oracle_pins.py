@@ -71,11 +71,14 @@ def test_philox_matches_numpy_random():
 
 # --------------------------------------------------------------- library ----
 def numpy_library(n_m, L, j, E, tau, k, seed):
-    """Random-key selection restated with numpy's Philox and Python sorting."""
+    """Random-key selection restated with numpy's Philox and Python sorting:
+    point m's key is 32-bit half m mod 8 (high half of word 0 first) of the
+    block at counter m // 8, then m."""
     keys = []
     for m in range(n_m):
-        w = int(numpy_philox_block([m, k, L, (j << 16) | (E << 8) | tau], [seed, 0])[0])
-        keys.append(((w >> 32) << 32) | m)
+        block = numpy_philox_block([m // 8, k, L, (j << 16) | (E << 8) | tau], [seed, 0])
+        halves = [h for w in block for h in (int(w) >> 32, int(w) & 0xFFFFFFFF)]
+        keys.append((halves[m % 8] << 32) | m)
     keys.sort()
     return np.array(sorted(x & 0xFFFFFFFF for x in keys[:L]), dtype=np.int32)
 
