@@ -151,6 +151,20 @@ struct UnitList {
   int64_t lib_total = 0, part_total = 0, order_total = 0, table_total = 0;
   int64_t order_scratch_total = 0;    // 64-bit keys for sorting manifolds above kOrderMaxSort
   int max_R = 0;
+  // Table jobs are sorted by R (sort_items) and built one launch per sort
+  // size (the power of two at or above R): a launch's shared memory per warp
+  // follows its own largest row, so short rows run more warps per SM.
+  static int table_rcap(int R) {
+    int rc = 32;
+    while (rc < R) rc <<= 1;
+    return rc;
+  }
+  int table_groups() const {
+    int g = 0;
+    for (size_t q = 0; q < tables.size(); ++q)
+      if (q == 0 || table_rcap(tables[q].R) != table_rcap(tables[q - 1].R)) ++g;
+    return g;
+  }
   double brute_flops = 0.0;           // 3E per pair of the units searched by brute force
   int table_u16() const { return max_nm < 65536 ? 1 : 0; }
   size_t table_elem() const { return table_u16() ? 2 : 4; }
@@ -400,6 +414,8 @@ void sort_by_cost(std::vector<WorkItem>* items, const std::vector<double>& cost)
 }
 
 void sort_items(UnitList* ul) {
+  std::stable_sort(ul->tables.begin(), ul->tables.end(),
+                   [](const TableJob& a, const TableJob& b) { return a.R < b.R; });
   // Brute-force items: grouped by E (one single-E kernel launch per group,
   // in the stream's order), larger items first within a group.
   {
@@ -686,11 +702,21 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                         reinterpret_cast<int32_t*>(base + ar.order),
                         reinterpret_cast<unsigned long long*>(base + ar.order_scratch), s));
   CCM_CUDA(enqueue_obs(base, ar, ul, s));
-  CCM_CUDA(launch_table_build(reinterpret_cast<const float*>(base + ar.series),
-                              reinterpret_cast<const TableJob*>(base + ar.tables),
-                              (int64_t)ul.tables.size(), ul.max_nm, ul.max_R,
-                              reinterpret_cast<const int32_t*>(base + ar.order),
-                              base + ar.table, ul.table_u16(), s));
+  for (size_t g0 = 0; g0 < ul.tables.size();) {  // one launch per sort size
+    const int rc = UnitList::table_rcap(ul.tables[g0].R);
+    size_t g1 = g0;
+    int nm = 0, rmax = 0;
+    for (; g1 < ul.tables.size() && UnitList::table_rcap(ul.tables[g1].R) == rc; ++g1) {
+      nm = std::max(nm, ul.tables[g1].n_m);
+      rmax = std::max(rmax, ul.tables[g1].R);
+    }
+    CCM_CUDA(launch_table_build(reinterpret_cast<const float*>(base + ar.series),
+                                reinterpret_cast<const TableJob*>(base + ar.tables) + g0,
+                                (int64_t)(g1 - g0), nm, rmax,
+                                reinterpret_cast<const int32_t*>(base + ar.order),
+                                base + ar.table, ul.table_u16(), s));
+    g0 = g1;
+  }
   if (ev) CCM_CUDA(record(ev[1]));
   SamplerParams sp = sampler_params(base, ar);
   sp.dbg_lib = dbg_lib;
@@ -983,7 +1009,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.table_bytes = pl->ul.table_elem() * (size_t)pl->ul.table_total;
   // launches of one ccm_run: order, tables, sampler, one brute-force and one
   // table-scan kernel per E present
-  in.launches_per_run = 3 + (pl->ul.tables.empty() ? 0 : 1);  // order, observed moments, sampler
+  in.launches_per_run = 3 + pl->ul.table_groups();  // order, observed moments, sampler, tables
   for (int E = 1; E <= kMaxE; ++E)
     in.launches_per_run += (pl->ul.e_count[E] > 0 ? 1 : 0) + (pl->ul.te_count[E] > 0 ? 1 : 0);
   *out = pl.release();

@@ -21,11 +21,12 @@
 // Build: one warp per query position.  A histogram of the top 11 bits of the
 // FP32 bit patterns of all N_m squared distances finds the bin b1 holding rank
 // R; a second pass collects every entry below b1 (all of them belong to the
-// row) and the entries of b1, which are sorted by (bits, index) to take the
-// rest.  When b1 holds more than kTableBoundary entries, two more radix
-// passes (11, 10 bits) refine it to the exact R-th value T instead and a
-// pass collects the entries below T and, in index order, the first ties.  A
-// bitonic sort in shared memory orders the R keys (bits << 32 | index).
+// row) and the entries of b1; both are sorted by (bits, index) (bitonic sorts
+// in shared memory), and the row is the entries below b1 followed by the
+// first of b1.  When b1 holds more than kTableBoundary entries, two more radix
+// passes (11, 10 bits) refine it to the exact R-th value T instead, a pass
+// collects the entries below T and, in index order, the first ties, and one
+// sort orders the R keys (bits << 32 | index).
 #include <stdint.h>
 
 #include "ccm_internal.h"
@@ -116,7 +117,7 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long* keys, int n) {
 template <int E>
 __device__ void build_row(const float* s, const TableJob& jb, int pos, const int32_t* order,
                           void* table, int u16, uint32_t* hist, unsigned long long* keys,
-                          unsigned long long* bnd) {
+                          unsigned long long* bnd, uint32_t* cnt) {
   const int lane = threadIdx.x & 31;
   const unsigned below_lane = (1u << lane) - 1u;
   const int n_m = jb.n_m, tau = jb.tau, off = (E - 1) * tau, R = jb.R;
@@ -140,23 +141,31 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
   if (in_b1 <= (uint32_t)kTableBoundary) {
     // Pass 2: every entry below b1 is a row entry; the entries of b1 are
     // sorted and the first R - below1 of them complete the row.
-    uint32_t nl = 0u, nb = 0u;
-    for (int base = 0; base < n_m; base += 32) {
-      const int x = base + lane;
-      const uint32_t bits = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
+    // positions by shared-memory atomics (the entries are rare): no warp vote
+    // in the loop, so consecutive iterations' loads overlap; both lists are
+    // sorted by their full keys below, so the arrival order does not matter
+    if (lane == 0) cnt[0] = cnt[1] = 0u;
+    __syncwarp();
+    for (int x = lane; x < n_m; x += 32) {
+      const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
       const uint32_t bin = bits >> 21;
-      const bool lt = x < n_m && bin < (uint32_t)b1, eq = x < n_m && bin == (uint32_t)b1;
-      const unsigned lm = __ballot_sync(kFullMask, lt), em = __ballot_sync(kFullMask, eq);
-      if (lt) keys[nl + __popc(lm & below_lane)] = key_of(bits, x);
-      if (eq) bnd[nb + __popc(em & below_lane)] = key_of(bits, x);
-      nl += __popc(lm);
-      nb += __popc(em);
+      if (bin < (uint32_t)b1) keys[atomicAdd(&cnt[0], 1u)] = key_of(bits, x);
+      else if (bin == (uint32_t)b1) bnd[atomicAdd(&cnt[1], 1u)] = key_of(bits, x);
     }
+    __syncwarp();
+    const uint32_t nb = cnt[1];
     int p2 = 32;
     while (p2 < (int)nb) p2 <<= 1;
     for (int i = (int)nb + lane; i < p2; i += 32) bnd[i] = ~0ull;
     __syncwarp();
     warp_bitonic(bnd, p2);
+    // every entry below b1 precedes every entry of b1: sort only those below
+    // (padded to a power of two), then append the boundary bin's first ones
+    int pl = 32;
+    while (pl < (int)below1) pl <<= 1;
+    for (int i = (int)below1 + lane; i < pl; i += 32) keys[i] = ~0ull;
+    __syncwarp();
+    warp_bitonic(keys, pl);
     for (int i = lane; i < R - (int)below1; i += 32) keys[below1 + i] = bnd[i];
   } else {
     // A crowded boundary bin: refine it with two more radix passes (11 and 10
@@ -200,12 +209,13 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
       less_seen += __popc(lm);
       ties_seen += __popc(tm);
     }
+    int rcap = 32;  // this row's sort size: the power of two at or above R
+    while (rcap < R) rcap <<= 1;
+    for (int i = R + lane; i < rcap; i += 32) keys[i] = ~0ull;
+    __syncwarp();
+    warp_bitonic(keys, rcap);
   }
-  int rcap = 32;  // this row's sort size: the power of two at or above R
-  while (rcap < R) rcap <<= 1;
-  for (int i = R + lane; i < rcap; i += 32) keys[i] = ~0ull;
   __syncwarp();
-  warp_bitonic(keys, rcap);
   const int64_t base = jb.table_off + (int64_t)pos * 4;
   if (u16) {
     uint16_t* out = static_cast<uint16_t*>(table) + base;
@@ -219,10 +229,11 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kTableWarps * 32)
+__global__ void __launch_bounds__(kTableWarps * 32, 2)
 table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
                    int u16, int rcap) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_cnt[kTableWarps][2];  // per warp: entries below b1, entries of b1
   const TableJob jb = jobs[blockIdx.y];
   const int warp = threadIdx.x >> 5;
   const int pos = blockIdx.x * kTableWarps + warp;
@@ -236,7 +247,7 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
   const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
   switch (jb.E) {
 #define CCM_TB(EV) \
-  case EV: build_row<EV>(s, jb, pos, order, table, u16, hist, keys, bnd); break;
+  case EV: build_row<EV>(s, jb, pos, order, table, u16, hist, keys, bnd, s_cnt[warp]); break;
     CCM_TB(1) CCM_TB(2) CCM_TB(3) CCM_TB(4) CCM_TB(5)
     CCM_TB(6) CCM_TB(7) CCM_TB(8) CCM_TB(9) CCM_TB(10)
 #undef CCM_TB
