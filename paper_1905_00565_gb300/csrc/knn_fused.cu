@@ -777,7 +777,9 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
 }
 
 template <int E>
-__global__ void __launch_bounds__(kThreads, 3) knn_table_kernel(KnnParams p) {
+// Four CTAs per SM (64 registers a thread): the table walk waits on L2, and
+// more resident warps hide more of it than the few spilled registers cost.
+__global__ void __launch_bounds__(kThreads, 4) knn_table_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ RingMeta s_meta[kRing];
