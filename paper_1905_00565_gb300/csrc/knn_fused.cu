@@ -174,6 +174,20 @@ __device__ __forceinline__ void insert_sorted(u64 (&ku)[K], u64 x) {
   ku[0] = below[0] ? x : ku[0];
 }
 
+// Insert key x into ku[0..K) when only ku[0..n) may hold keys (the rest are
+// the empty key): the same result as insert_sorted, with the comparisons of
+// slots past n folded away when n is a compile-time constant.
+template <int K>
+__device__ __forceinline__ void insert_prefix(u64 (&ku)[K], u64 x, int n) {
+  bool below[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) below[s] = (s <= n) && x < ku[s];
+#pragma unroll
+  for (int s = K - 1; s > 0; --s)
+    if (s <= n) ku[s] = below[s - 1] ? ku[s - 1] : (below[s] ? x : ku[s]);
+  ku[0] = below[0] ? x : ku[0];
+}
+
 // Butterfly sum over the warp: every lane ends with the same bits (each
 // level adds the same two values in either order).
 __device__ __forceinline__ double warp_sum(double v) {
@@ -463,6 +477,8 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   constexpr int kPairs = kStep / 2;
   // merge trigger: at most kBuf - kStep + 1 so that a step can always append
   const int merge_at = max(1, min(p.merge_at[E], kBuf - kStep + 1));
+  // the first kInit points of the order go straight into the empty list
+  constexpr int kInit = (K + kStep - 1) / kStep * kStep;
 
   // A warp's 32 queries are consecutive positions of the query order.
   const int pos = tile * kQT + tid;
@@ -548,8 +564,26 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
     }
     __syncthreads();
 
+    int a_first = 0;
+    if (t0 == 0) {
+      // The first kInit points (near this tile: the scan starts there) fill
+      // the list directly, each inserted into a list of known length; the
+      // threshold is then finite before the first candidate is appended.
+#pragma unroll
+      for (int pp = 0; pp < kInit / 2; ++pp) {
+        float d2[2];
+        unpack2(sqdist2_range<E, 0, E>(qc, s_coord + (size_t)pp * EP, 0ull), d2[0], d2[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int l = s_lidx[2 * pp + h];
+          const u64 key = (abs(l - m) > W) ? pack_key(d2[h], l) : pack_key(INFINITY, INT_MAX);
+          insert_prefix<K>(ku, key, 2 * pp + h);
+        }
+      }
+      a_first = kInit;
+    }
 #pragma unroll 1
-    for (int a = 0; a < ntp; a += kStep) {
+    for (int a = a_first; a < ntp; a += kStep) {
       if ((a & (kChunk - 1)) == 0) {
         // Chunk pruning.  gap_e = max(0, lo_e - qhi_e, qlo_e - hi_e) bounds
         // |q_e - x_e| from below for every query q of the warp and point x of
