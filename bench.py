@@ -344,7 +344,8 @@ def run_ours(args, rank, world, local_rank):
                                     "groups, z > 1.645"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": traffic_entry(),
+                         # the committed capture covers the sweep workload only
+                         "traffic": traffic_entry() if args.workload == "sweep" else None,
                          "traffic_unit": "DRAM bytes per step, all brute-force launches "
                                          "(ncu, scaled from an r=8 capture)",
                          "algorithmic_bytes": "4L per realization (library indices) + 8 (rho)",
