@@ -83,7 +83,8 @@ typedef struct {
   int32_t n_series;        /* V >= 2 series, each of length n */
   int64_t n;               /* series length N */
   int32_t n_pairs;         /* number of (j, i) pairs */
-  const int32_t* pairs;    /* [n_pairs][2] = (library var j, target var i), 0 <= i, j < V, i != j */
+  const int32_t* pairs;    /* [n_pairs][2] = (library var j, target var i), 0 <= i, j < V, i != j;
+                              (pairs sharing a j) x ceil(n/256) must stay below 2^31 */
   int32_t n_E;
   const int32_t* E;        /* [n_E], each 1..10 */
   int32_t n_tau;

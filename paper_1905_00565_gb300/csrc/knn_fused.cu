@@ -25,14 +25,17 @@
 //    a small per-query buffer in shared memory and merged, warp-wide, when a
 //    buffer runs full, so a rare insertion in one lane does not stall the
 //    warp for a full sorted insertion every time;
-//  * the library is visited in ascending manifold index, so a strict "<"
-//    during insertion keeps equal distances in index order;
+//  * the library is visited in query order from the run nearest the tile
+//    (wrapping around), so candidates are compared by the packed key
+//    (squared distance, index): equal distances keep index order whatever
+//    the visiting order;
 //  * the epilogue forms u_i = exp(-d_i/d_1) (optionally floored), the
-//    prediction, and the tile's FP64 moments (one warp does the FP64 work:
-//    the FP64 pipe is the scarce unit; the observed values' half of it is
-//    done once per (j, i, E, tau) by obs_kernel, not once per realization);
-//    the last tile of a realization to finish merges the tiles' moments in a
-//    fixed order, so rho does not depend on the schedule.
+//    prediction, and the FP64 moments of each (tile, target): predictions go
+//    to a shared-memory ring whose eight slots are reduced by eight warps at
+//    once (the FP64 pipe is the scarce unit); the observed values' half is
+//    done once per (j, i, E, tau) by obs_kernel, not once per realization;
+//    the last (tile, target) of a realization to finish merges the tiles'
+//    moments in a fixed order, so rho does not depend on the schedule.
 #include <float.h>
 #include <limits.h>
 #include <math.h>

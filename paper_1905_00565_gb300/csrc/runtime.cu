@@ -106,6 +106,15 @@ ccm_status copy_problem(const ccm_problem* p, ProblemCopy* pc) {
     if (j < 0 || j >= pc->V || i < 0 || i >= pc->V || i == j)
       return fail(CCM_EINVAL, "pair " + std::to_string(q) + " is invalid (need 0<=i,j<V, i!=j)");
   }
+  {
+    // a realization completes after (query tiles) x (targets of its library
+    // variable) reductions, counted in 32 bits
+    std::map<int32_t, int64_t> targets_of;
+    int64_t most = 0;
+    for (int32_t q = 0; q < p->n_pairs; ++q) most = std::max(most, ++targets_of[pc->pairs[2 * q]]);
+    if (most * ((pc->n + 255) / 256) > 0x7fffffff)
+      return fail(CCM_EINVAL, "targets of one library variable x query tiles exceed 2^31 - 1");
+  }
   for (int32_t E : pc->E)
     if (E < 1 || E > kMaxE) return fail(CCM_EINVAL, "E must be in 1..10");
   for (int32_t t : pc->tau)
