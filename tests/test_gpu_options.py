@@ -132,3 +132,19 @@ def test_invalid_options_are_refused(ccm):
             assert ei.value.status == ccm.CCM_EINVAL
     finally:
         ccm.ccm_context_destroy(ctx)
+
+
+def test_completion_count_range_is_checked(ccm):
+    """A realization completes after (query tiles) x (targets of its library
+    variable) reductions, counted in 32 bits: a problem reaching 2^31 is
+    refused before anything is allocated (only the series shape is given)."""
+    n = 2**31 - 1                                # ceil(n/256) = 8388608 tiles
+    many = np.array([[0, i] for i in range(1, 257)], np.int32)   # 256 targets of j = 0
+    ctx = ccm.ccm_context_create(0)
+    try:
+        with pytest.raises(ccm.CCMError) as ei:
+            ccm.ccm_plan(ctx, (257, n), many, [2], [1], [10], 1, 1)
+        assert ei.value.status == ccm.CCM_EINVAL
+        assert "2^31" in str(ei.value)
+    finally:
+        ccm.ccm_context_destroy(ctx)
