@@ -156,7 +156,6 @@ cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_
 // Fused kernel (knn_fused.cu).
 int knn_block_threads();
 int knn_queries_per_thread();
-size_t knn_smem_bytes(int emin, int emax);
 cudaError_t knn_prepare();
 cudaError_t knn_occupancy(int E, int* ctas_per_sm);
 cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s);

@@ -923,7 +923,6 @@ cudaError_t launch_obs(const float* series, const int32_t* order, const ObsJob* 
   obs_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(series, order, jobs, n_jobs, n_tiles, obs);
   return cudaGetLastError();
 }
-size_t knn_smem_bytes(int, int) { return kSmemBytes; }
 
 // One kernel per E (each keeps all its registers for that E's lists).
 

@@ -159,7 +159,6 @@ struct UnitList {
   std::vector<double> item_cost_table;
   int64_t lib_total = 0, part_total = 0, order_total = 0, table_total = 0;
   int64_t order_scratch_total = 0;    // 64-bit keys for sorting manifolds above kOrderMaxSort
-  int max_R = 0;
   // Table jobs are sorted by R (sort_items) and built one launch per sort
   // size (the power of two at or above R): a launch's shared memory per warp
   // follows its own largest row, so short rows run more warps per SM.
@@ -331,7 +330,6 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
           tj.R = (int32_t)R;
           table_of[std::make_tuple(j, E, tau)] = std::make_pair(tj.table_off, tj.R);
           ul->table_total += n_m * R;
-          ul->max_R = std::max(ul->max_R, (int)R);
           ul->tables.push_back(tj);
         }
   }
