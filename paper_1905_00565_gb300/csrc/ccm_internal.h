@@ -113,6 +113,7 @@ struct KnnParams {
   const int32_t* lib;
   const int32_t* order;   // query order (manifold index per position)
   const void* table;      // distance indexing tables (units with table_R > 0)
+  const float* table_d2;  // the FP32 squared distance of every table entry, same layout
   int32_t table_u16;      // 1: uint16 entries (every manifold below 65536 points), 0: int32
   double* partials;       // 6 doubles per query tile
   const double* obs;      // observed-moment tile records (TargetDesc::obs_tile)
@@ -151,7 +152,7 @@ cudaError_t launch_order(const float* series, const OrderJob* jobs, int64_t n_jo
 cudaError_t table_prepare();
 cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs,
                                int max_nm, int max_R, const int32_t* order, void* table,
-                               int table_u16, cudaStream_t s);
+                               float* table_d2, int table_u16, cudaStream_t s);
 
 // Fused kernel (knn_fused.cu).
 int knn_block_threads();

@@ -690,6 +690,10 @@ __device__ __forceinline__ float d2_point(const float* sj, int off, int tau, con
 // kByteMapMax points (a load and a compare per table entry), else one bit.
 constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
 constexpr int kByteMapMax = 32768;
+// A hit is stored as (rank << kHitRankShift) | manifold index.
+constexpr int kHitRankShift = 20;
+static_assert(kTableMaxNm <= (1 << kHitRankShift), "manifold index must fit below the rank");
+static_assert(kTableMaxR <= (1 << (31 - kHitRankShift)), "rank must fit in the hit word");
 
 template <int E>
 __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
@@ -768,15 +772,25 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
         const int q4 = (c & 2) ? hi : lo, q4b = (c & 2) ? hi2 : lo2;
         const int xc = (c & 4) ? q4b : q4;
         if (abs(xc - m) > W) {
-          s_hit[found * kThreads + tid] = xc;
+          s_hit[found * kThreads + tid] = ((4 * g + c) << kHitRankShift) | xc;  // rank, index
           ++found;
         }
       }
     }
     int nb[E + 1];
+    float dd[E + 1];
     if (found > E) {
+      // the neighbours' squared distances are read from the table (the same
+      // bits as recomputing them: the build used the same rounding sequence)
 #pragma unroll
-      for (int s2 = 0; s2 <= E; ++s2) nb[s2] = valid ? s_hit[s2 * kThreads + tid] : 0;
+      for (int s2 = 0; s2 <= E; ++s2) {
+        const int h = valid ? s_hit[s2 * kThreads + tid] : 0;
+        const int rank = h >> kHitRankShift;
+        nb[s2] = h & ((1 << kHitRankShift) - 1);
+        dd[s2] = valid ? __ldg(p.table_d2 + u.table_off + (int64_t)(rank >> 2) * 4 * n_m + col +
+                               (rank & 3))
+                       : 0.f;
+      }
     } else {
       // Rare: fewer than E+1 members among the R nearest points; scan the
       // library, keeping the E+1 smallest (distance, index) keys.
@@ -803,12 +817,11 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
         }
       }
 #pragma unroll
-      for (int s2 = 0; s2 <= E; ++s2) nb[s2] = kl[s2];
+      for (int s2 = 0; s2 <= E; ++s2) {
+        nb[s2] = kl[s2];
+        dd[s2] = valid ? kd[s2] : 0.f;
+      }
     }
-    float dd[E + 1];
-#pragma unroll
-    for (int s2 = 0; s2 <= E; ++s2)
-      dd[s2] = valid ? d2_point<E>(sj, off, tau, q, max(nb[s2], 0)) : 0.f;
     finish_tile<E, false>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr);
   }
 }

@@ -314,7 +314,8 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
                       2 * (int64_t)pc.theiler;
           // whole groups of four ranks (the table's layout)
           R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR), n_m / 4 * 4);
-          const double bytes = (double)n_m * (double)R * (n_m < 65536 ? 2.0 : 4.0);
+          // indices (2 or 4 bytes) and FP32 squared distances
+          const double bytes = (double)n_m * (double)R * ((n_m < 65536 ? 2.0 : 4.0) + 4.0);
           if (table_bytes + bytes > table_cap_bytes) continue;
           table_bytes += bytes;
           TableJob tj;
@@ -477,7 +478,7 @@ void sort_items(UnitList* ul) {
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
          counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
-         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, total = 0;
+         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_d2 = 0, total = 0;
 };
 
 Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
@@ -503,6 +504,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.orders = take(sizeof(OrderJob) * ul.orders.size());
   a.targets = take(sizeof(TargetDesc) * ul.targets.size());
   a.table = take(ul.table_elem() * (size_t)ul.table_total);
+  a.table_d2 = take(sizeof(float) * (size_t)ul.table_total);
   a.tables = take(sizeof(TableJob) * ul.tables.size());
   a.items_table = take(sizeof(WorkItem) * ul.items_table.size());
   a.obs = take(sizeof(double) * kObsStride * (size_t)ul.obs_total);
@@ -662,6 +664,7 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.lib = reinterpret_cast<const int32_t*>(base + ar.lib);
   kp.order = reinterpret_cast<const int32_t*>(base + ar.order);
   kp.table = base + ar.table;
+  kp.table_d2 = reinterpret_cast<const float*>(base + ar.table_d2);
   kp.table_u16 = ul.table_u16();
   kp.partials = reinterpret_cast<double*>(base + ar.part);
   kp.obs = reinterpret_cast<const double*>(base + ar.obs);
@@ -721,7 +724,8 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                                 reinterpret_cast<const TableJob*>(base + ar.tables) + g0,
                                 (int64_t)(g1 - g0), nm, rmax,
                                 reinterpret_cast<const int32_t*>(base + ar.order),
-                                base + ar.table, ul.table_u16(), s));
+                                base + ar.table, reinterpret_cast<float*>(base + ar.table_d2),
+                                ul.table_u16(), s));
     g0 = g1;
   }
   if (ev) CCM_CUDA(record(ev[1]));
@@ -1013,7 +1017,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.pair_count = pl->ul.pairs;
   in.flop_count = pl->ul.flops;
   in.brute_flop_count = pl->ul.brute_flops;
-  in.table_bytes = pl->ul.table_elem() * (size_t)pl->ul.table_total;
+  in.table_bytes = (pl->ul.table_elem() + sizeof(float)) * (size_t)pl->ul.table_total;
   // launches of one ccm_run: order, tables, sampler, one brute-force and one
   // table-scan kernel per E present
   in.launches_per_run = 3 + pl->ul.table_groups();  // order, observed moments, sampler, tables

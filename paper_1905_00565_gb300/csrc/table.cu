@@ -16,7 +16,10 @@
 // r%4], so that one 8-byte (16-bit entries) or 16-byte (32-bit) load gives a
 // query four consecutive ranks and the 32 consecutive query positions of a
 // warp read one group with one coalesced access; 16-bit entries when every
-// manifold of the plan has fewer than 65536 points, else 32-bit.
+// manifold of the plan has fewer than 65536 points, else 32-bit.  A float
+// array of the same layout holds each entry's squared distance, so that the
+// scan reads the E+1 distances it needs instead of recomputing them from E
+// scattered coordinates each.
 //
 // Build: one warp per query position.  A histogram of the top 11 bits of the
 // FP32 bit patterns of all N_m squared distances finds the bin b1 holding rank
@@ -116,7 +119,8 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long* keys, int n) {
 
 template <int E>
 __device__ void build_row(const float* s, const TableJob& jb, int pos, const int32_t* order,
-                          void* table, int u16, uint32_t* hist, unsigned long long* keys,
+                          void* table, float* table_d2, int u16, uint32_t* hist,
+                          unsigned long long* keys,
                           unsigned long long* bnd, uint32_t* cnt) {
   const int lane = threadIdx.x & 31;
   const unsigned below_lane = (1u << lane) - 1u;
@@ -217,6 +221,8 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
   }
   __syncwarp();
   const int64_t base = jb.table_off + (int64_t)pos * 4;
+  for (int r = lane; r < R; r += 32)  // each entry's squared distance, beside it
+    table_d2[base + (int64_t)(r >> 2) * 4 * n_m + (r & 3)] = __uint_as_float((uint32_t)(keys[r] >> 32));
   if (u16) {
     uint16_t* out = static_cast<uint16_t*>(table) + base;
     for (int r = lane; r < R; r += 32)
@@ -231,7 +237,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
 
 __global__ void __launch_bounds__(kTableWarps * 32, 2)
 table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
-                   int u16, int rcap) {
+                   float* table_d2, int u16, int rcap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_cnt[kTableWarps][2];  // per warp: entries below b1, entries of b1
   const TableJob jb = jobs[blockIdx.y];
@@ -247,7 +253,7 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
   const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
   switch (jb.E) {
 #define CCM_TB(EV) \
-  case EV: build_row<EV>(s, jb, pos, order, table, u16, hist, keys, bnd, s_cnt[warp]); break;
+  case EV: build_row<EV>(s, jb, pos, order, table, table_d2, u16, hist, keys, bnd, s_cnt[warp]); break;
     CCM_TB(1) CCM_TB(2) CCM_TB(3) CCM_TB(4) CCM_TB(5)
     CCM_TB(6) CCM_TB(7) CCM_TB(8) CCM_TB(9) CCM_TB(10)
 #undef CCM_TB
@@ -266,14 +272,14 @@ cudaError_t table_prepare() {
 
 cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs,
                                int max_nm, int max_R, const int32_t* order, void* table,
-                               int table_u16, cudaStream_t s) {
+                               float* table_d2, int table_u16, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
   int rcap = 32;
   while (rcap < max_R) rcap <<= 1;
   if (rcap > kTableMaxR) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((max_nm + kTableWarps - 1) / kTableWarps), (unsigned)n_jobs);
-  table_build_kernel<<<grid, kTableWarps * 32, table_smem(rcap), s>>>(series, jobs, order, table,
-                                                                      table_u16, rcap);
+  table_build_kernel<<<grid, kTableWarps * 32, table_smem(rcap), s>>>(
+      series, jobs, order, table, table_d2, table_u16, rcap);
   return cudaGetLastError();
 }
 
