@@ -71,6 +71,10 @@ def _load():
                                                 ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_double, _I32P, _F64P]
             lib.oracle_query_subset.restype = ctypes.c_int
+            lib.oracle_query_margin.argtypes = [_F32P, ctypes.c_int64, ctypes.c_int32,
+                                                ctypes.c_int32, _I32P, ctypes.c_int64, _I64P,
+                                                ctypes.c_int64, ctypes.c_int32, _F64P]
+            lib.oracle_query_margin.restype = ctypes.c_int
             lib.oracle_pearson.argtypes = [_F64P, _F64P, ctypes.c_int64]
             lib.oracle_pearson.restype = ctypes.c_double
             lib.oracle_skill.argtypes = [_F32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -173,6 +177,24 @@ def query_subset(lib_s: np.ndarray, tgt_s: np.ndarray, E: int, tau: int, lib: np
     if rc != 0:
         raise ValueError("invalid query subset arguments")
     return nbr, xh
+
+
+def query_margin(s: np.ndarray, E: int, tau: int, lib: np.ndarray, queries,
+                 theiler: int = 0) -> np.ndarray:
+    """Per listed query, the relative FP64 gap (d_b - d_a) / d_b between its
+    (E+1)-th and (E+2)-th nearest candidate distances (inf with only E+1
+    candidates, 0 when d_b = 0): a neighbour set chosen in FP32 may differ
+    from the FP64 one only where this gap is small."""
+    s = _c(s, np.float32)
+    lib = _c(lib, np.int32)
+    q = _c(queries, np.int64)
+    out = np.zeros(len(q), np.float64)
+    rc = _load().oracle_query_margin(_ptr(s, _F32P), len(s), int(E), int(tau), _ptr(lib, _I32P),
+                                     len(lib), _ptr(q, _I64P), len(q), int(theiler),
+                                     _ptr(out, _F64P))
+    if rc != 0:
+        raise ValueError("invalid margin arguments")
+    return out
 
 
 def pearson(x: np.ndarray, y: np.ndarray) -> float:

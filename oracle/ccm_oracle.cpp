@@ -359,6 +359,41 @@ int oracle_query_subset(const float* lib_s, const float* tgt_s, int64_t n, int32
   return 0;
 }
 
+// How close query m's neighbour set is to a tie at its boundary: the FP64
+// distances (selection in FP64) of its (E+1)-th and (E+2)-th nearest
+// candidates, d_a <= d_b, give gap = (d_b - d_a) / d_b; +inf when the query
+// has only E+1 candidates, 0 when d_b = 0.  A neighbour set chosen in a lower
+// precision can differ from the FP64 one only where this gap is small: the
+// point swapped out is no farther than d_a and the point swapped in no
+// nearer than d_b in FP64, yet the two compared the other way.
+int oracle_query_margin(const float* s, int64_t n, int32_t E, int32_t tau, const int32_t* lib,
+                        int64_t L, const int64_t* queries, int64_t nq, int32_t theiler,
+                        double* gap_out) {
+  const int64_t n_m = n - (int64_t)(E - 1) * tau;
+  if (E < 1 || tau < 1 || n_m < 1 || L < E + 2 || L > n_m) return -1;
+  if (!options_ok(E, L, theiler, 0.0)) return -1;
+  std::vector<double> d2;
+  d2.reserve((size_t)L);
+  for (int64_t q = 0; q < nq; ++q) {
+    const int64_t m = queries[q];
+    if (m < 0 || m >= n_m) return -1;
+    d2.clear();
+    for (int64_t a = 0; a < L; ++a) {
+      const int32_t l = lib[a];
+      if (std::llabs((long long)l - (long long)m) <= theiler) continue;
+      d2.push_back(sqdist_fp64(s, E, tau, m, l));
+    }
+    if ((int64_t)d2.size() < E + 2) {
+      gap_out[q] = INFINITY;
+      continue;
+    }
+    std::partial_sort(d2.begin(), d2.begin() + (E + 2), d2.end());
+    const double da = std::sqrt(d2[(size_t)E]), db = std::sqrt(d2[(size_t)E + 1]);
+    gap_out[q] = (db > 0.0) ? (db - da) / db : 0.0;
+  }
+  return 0;
+}
+
 double oracle_pearson(const double* x, const double* y, int64_t n) { return pearson(x, y, n); }
 
 // Pearson rho of observed target vs predictions given as FP64 [N_m].

@@ -373,10 +373,57 @@ def test_fp32_selection_differs_from_fp64_only_at_near_ties():
             lib = oracle.library(n_m, 300, 1, E, tau, k, 12)
             a = oracle.neighbours(s[1], E, tau, lib, select_fp64=False)
             b = oracle.neighbours(s[1], E, tau, lib, select_fp64=True)
-            for m in np.nonzero(np.any(np.sort(a, 1) != np.sort(b, 1), axis=1))[0]:
+            rows = np.nonzero(np.any(np.sort(a, 1) != np.sort(b, 1), axis=1))[0]
+            for m in rows:
                 d = sorted(math.sqrt(_sqdist64(s[1], E, tau, int(m), int(l)))
                            for l in lib if l != m)
-                assert (d[E + 1] - d[E]) <= 1e-6 * d[E]
+                assert (d[E + 1] - d[E]) <= 1e-6 * d[E + 1]
+            if len(rows):
+                assert np.all(oracle.query_margin(s[1], E, tau, lib, rows) < 1e-6)
+
+
+def brute_margin(s, E, tau, lib, m, theiler=0):
+    """Pure-Python relative FP64 gap between the (E+1)-th and (E+2)-th nearest
+    candidate distances of query m (inf with only E+1 candidates, 0 at d_b = 0)."""
+    d2 = sorted(_sqdist64(s, E, tau, m, int(l)) for l in lib if abs(int(l) - m) > theiler)
+    if len(d2) < E + 2:
+        return math.inf
+    da, db = math.sqrt(d2[E]), math.sqrt(d2[E + 1])
+    return (db - da) / db if db > 0.0 else 0.0
+
+
+@pytest.mark.parametrize("kind", ["uniform", "integers", "logistic"])
+def test_query_margin_matches_brute_force(kind):
+    rng = np.random.default_rng(hash(kind) & 0xFFFF)
+    for E in range(1, 5):
+        for tau in range(1, 4):
+            n = int(rng.integers(E * tau + 12, 41))
+            s = _tiny_series(kind, n, rng)
+            n_m = n - (E - 1) * tau
+            for W in (0, 2):
+                for L in sorted({E + 2 + 2 * W, n_m}):
+                    lib = np.sort(rng.choice(n_m, size=L, replace=False)).astype(np.int32)
+                    q = np.arange(n_m)
+                    got = oracle.query_margin(s, E, tau, lib, q, theiler=W)
+                    want = [brute_margin(s, E, tau, lib, int(m), W) for m in q]
+                    assert np.array_equal(got, np.array(want)), (kind, E, tau, L, W)
+
+
+def test_query_margin_closed_forms():
+    """E = 1 on the values 0, 1, 3, 6, 10, 15: from point 0 the candidates lie at
+    1, 3, 6, 10, 15, so the 2nd and 3rd nearest give (6 - 3)/6 = 1/2; from point 2
+    (value 3) they lie at 2, 3, 3, 7, 12: (3 - 3)/3 = 0 (an exact tie).  With only
+    E+1 = 2 candidates the set cannot be contested: inf.  A duplicate-heavy series
+    gives d_b = 0: 0."""
+    s = np.array([0, 1, 3, 6, 10, 15], np.float32)
+    lib = np.arange(6, dtype=np.int32)
+    g = oracle.query_margin(s, 1, 1, lib, [0, 2])
+    assert g[0] == 0.5 and g[1] == 0.0
+    assert oracle.query_margin(s, 1, 1, np.array([0, 1, 2], np.int32), [0])[0] == math.inf
+    z = np.array([1, 1, 1, 1, 5], np.float32)
+    assert oracle.query_margin(z, 1, 1, np.arange(5, dtype=np.int32), [0])[0] == 0.0
+    with pytest.raises(ValueError):
+        oracle.query_margin(s, 1, 1, lib, [6])
 
 
 # --------------------------------------------------------------- dynamics ---
