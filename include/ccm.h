@@ -234,7 +234,9 @@ ccm_status ccm_job_times(ccm_context* ctx, uint64_t ticket, double* submit_s, do
  * capture.  Every call reuses the same array: calls that overlap on the GPU
  * (several streams or host threads) race and must be serialised by the
  * caller.  cuda_stream NULL: runs on the default stream and blocks until done,
- * then reports kernel error flags; otherwise asynchronous. */
+ * then reports kernel error flags (CCM_ECUDA).  Otherwise asynchronous, and
+ * kernel error flags are NOT reported: the next call's set-up clears them, so
+ * an asynchronous caller that needs the check must pass NULL. */
 ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, int64_t n, int32_t j,
                            int32_t i, int32_t E, int32_t tau, int64_t L, int32_t r,
                            uint64_t seed, double* d_rho, void* cuda_stream);

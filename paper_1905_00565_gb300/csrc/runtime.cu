@@ -1355,6 +1355,7 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
   CCM_CUDA(cudaMemcpyAsync(b->h_err, base + b->ar.err, sizeof(int32_t), cudaMemcpyDeviceToHost,
                            b->stream));
   CCM_CUDA(cudaFreeAsync(b->d_arena, b->stream));
+  b->d_arena = nullptr;  // freed in stream order: the error path must not free it again
   CCM_CUDA(cudaLaunchHostFunc(b->stream, on_batch_done, b));
   return CCM_OK;
 }

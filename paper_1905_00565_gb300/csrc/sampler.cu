@@ -74,10 +74,13 @@ __device__ __forceinline__ uint32_t key_hi(const UnitDesc& u, int m) {
 // warp by warp: warp w walks its contiguous segment 32 positions at a time
 // (coalesced reads), counts members with a ballot, and after a block scan of
 // the warp counts writes them in position order.  item(q) gives the manifold
-// point at position q; is_member(m) decides membership.
+// point at position q; is_member(m) decides membership.  `out` has room for
+// `expect` entries: when the members number anything else (a sampler fault)
+// nothing is compacted and out[0..expect) is filled with point 0 instead, so
+// that later kernels reading the library stay in bounds.
 template <typename Item, typename Member>
 __device__ uint32_t block_compact(int n, Item item, Member is_member, int32_t* out,
-                                  uint32_t* s_warp) {
+                                  uint32_t expect, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int seg = ((n + nwarps - 1) / nwarps + 31) / 32 * 32;
@@ -95,6 +98,10 @@ __device__ uint32_t block_compact(int n, Item item, Member is_member, int32_t* o
     total += s_warp[w];
   }
   __syncthreads();
+  if (total != expect) {
+    for (uint32_t q = threadIdx.x; q < expect; q += blockDim.x) out[q] = 0;
+    return total;
+  }
   for (int q = q0 + lane; q - lane < q1; q += 32) {
     const int m = q < q1 ? item(q) : 0;
     const bool mem = q < q1 && is_member(m);
@@ -220,8 +227,8 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
   };
   // The library in query order (the order the neighbour search visits it in).
   const int32_t* ord = p.order + u.order_off;
-  const uint32_t total =
-      block_compact(n_m, [&](int q) { return ord[q]; }, is_member, p.lib + u.lib_off, s_warp);
+  const uint32_t total = block_compact(n_m, [&](int q) { return ord[q]; }, is_member,
+                                       p.lib + u.lib_off, (uint32_t)L, s_warp);
   if (total != (uint32_t)L) {  // not a permutation, or a lost tie: report, never guess
     if (threadIdx.x == 0) atomicOr(p.err, kErrSampler);
     return;
@@ -230,7 +237,7 @@ sampler_kernel(SamplerParams p, int64_t first_unit) {
     for (int t = 0; t < u.n_targets; ++t) {
       __syncthreads();
       block_compact(n_m, [](int q) { return q; }, is_member,
-                    p.dbg_lib + p.targets[u.tgt_off + t].lib_dbg_off, s_warp);
+                    p.dbg_lib + p.targets[u.tgt_off + t].lib_dbg_off, (uint32_t)L, s_warp);
     }
   }
 }
