@@ -78,6 +78,9 @@ typedef enum {
                                       each ccm_plan; default 4: table row length over the
                                       expected scan length) and CCM_TABLE_CROSSOVER (read
                                       once; default 190: tables for L >= sqrt(c*N_m/(E+1))) */
+#define CCM_SEARCH_STATS     0x20u /* the neighbour-search kernels also count their work
+                                      (ccm_plan_search_stats); a separately compiled
+                                      counting variant, slower, same results */
 
 typedef struct {
   int32_t n_series;        /* V >= 2 series, each of length n */
@@ -94,7 +97,8 @@ typedef struct {
   int32_t r;               /* realizations per (pair, E, tau, L) cell, >= 1 */
   uint64_t seed;           /* library sampler seed */
   uint32_t flags;          /* CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE | CCM_NO_AUTOTUNE |
-                              CCM_NO_TABLE; other bits are refused (CCM_EINVAL) */
+                              CCM_NO_TABLE | CCM_SEARCH_STATS; other bits are refused
+                              (CCM_EINVAL) */
   /* Two options the paper does not discuss (common CCM variants); zero for the
    * paper's method.  theiler: exclusion window W >= 0, library point l is a
    * neighbour candidate of query m only when |l - m| > W (W = 0 excludes m
@@ -128,6 +132,7 @@ typedef struct {
   double brute_flop_count;    /* the part of flop_count searched by brute force */
   size_t table_bytes;         /* distance indexing tables of the plan (0: none) */
   int64_t launches_per_run;   /* kernel launches of one ccm_run (graph nodes) */
+  double brute_pair_count;    /* the part of pair_count searched by brute force */
 } ccm_plan_info;
 
 typedef struct ccm_context ccm_context;
@@ -187,6 +192,28 @@ ccm_status ccm_plan_kernel_times(const ccm_plan_t* plan, double* sampler_ms, dou
  * moments + distance indexing tables, [1] library sampler, [2] brute-force fused kernel, [3] table-scan
  * fused kernel (0 when the stage launched nothing). */
 ccm_status ccm_plan_stage_times(const ccm_plan_t* plan, double* stage_ms /* [4] */);
+
+/* Work counts of the neighbour search in the plan's last completed run
+ * (plans made with CCM_SEARCH_STATS only; CCM_EINVAL otherwise).  They say how
+ * much of the method's exhaustive work (N_m*L pairs per realization) the
+ * brute-force kernels executed and what the selection cost.  Call after the
+ * run has finished. */
+typedef struct {
+  uint64_t brute_tiles;      /* query tiles (256 queries) searched by brute force */
+  uint64_t brute_queries;    /* their valid queries */
+  uint64_t pairs_begun;      /* query-library pairs whose squared distance was begun (the
+                                first coordinates of a step, before early termination) */
+  uint64_t pairs_full;       /* pairs whose squared distance was completed (all E) */
+  uint64_t pairs_pruned;     /* pairs skipped whole by the chunk bounding-box test */
+  uint64_t candidates;       /* pairs below a query's running threshold, queued for insertion */
+  uint64_t merge_slots;      /* insertion slots executed: per warp merge, 32 x the largest
+                                queue of its lanes (lanes with shorter queues idle) */
+  uint64_t table_queries;    /* queries answered from a distance indexing table */
+  uint64_t table_entries;    /* table entries loaded by those queries' walks */
+  uint64_t table_fallbacks;  /* of them, queries that met too few library members in their
+                                row and scanned their library instead */
+} ccm_search_stats;
+ccm_status ccm_plan_search_stats(const ccm_plan_t* plan, ccm_search_stats* out);
 
 /* The plain comparator: one sampler launch and one naive kNN launch per
  * realization (thread per query, library read from global memory, sorted

@@ -35,6 +35,7 @@ CCM_INPUT_ON_DEVICE = 0x1
 CCM_OUTPUT_ON_DEVICE = 0x2
 CCM_NO_AUTOTUNE = 0x4
 CCM_NO_TABLE = 0x10
+CCM_SEARCH_STATS = 0x20
 
 STATUS_NAMES = {0: "CCM_OK", 1: "CCM_PENDING", -1: "CCM_EINVAL", -2: "CCM_ENOMEM",
                 -3: "CCM_ETOOLARGE", -4: "CCM_ECUDA", -5: "CCM_ETIMEOUT",
@@ -45,7 +46,7 @@ EXPORTED = ["ccm_context_create", "ccm_context_destroy", "ccm_plan", "ccm_plan_d
             "ccm_plan_get_info", "ccm_run", "ccm_run_ex", "ccm_run_plain", "ccm_submit",
             "ccm_poll", "ccm_cancel", "ccm_job_times", "ccm_last_error", "ccm_version",
             "ccm_plan_kernel_times", "ccm_run_noalloc", "ccm_plan_stage_times",
-            "ccm_convergence"]
+            "ccm_convergence", "ccm_plan_search_stats"]
 
 
 class ccm_problem(ctypes.Structure):
@@ -69,7 +70,14 @@ class ccm_plan_info(ctypes.Structure):
                 ("n_work_items", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("pair_count", ctypes.c_double), ("flop_count", ctypes.c_double),
                 ("brute_flop_count", ctypes.c_double), ("table_bytes", ctypes.c_size_t),
-                ("launches_per_run", ctypes.c_int64)]
+                ("launches_per_run", ctypes.c_int64), ("brute_pair_count", ctypes.c_double)]
+
+
+class ccm_search_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in
+                ("brute_tiles", "brute_queries", "pairs_begun", "pairs_full", "pairs_pruned",
+                 "candidates", "merge_slots", "table_queries", "table_entries",
+                 "table_fallbacks")]
 
 
 class CCMError(RuntimeError):
@@ -105,6 +113,7 @@ def _load():
         "ccm_run_noalloc": ([vp, i32, i64, i32, i32, i32, i32, i64, i32, u64, vp, vp], st),
         "ccm_convergence": ([vp, vp, i64, i32, vp, i32, ctypes.c_double, vp, ctypes.c_uint32,
                              vp], st),
+        "ccm_plan_search_stats": ([vp, ctypes.POINTER(ccm_search_stats)], st),
         "ccm_last_error": ([], ctypes.c_char_p),
         "ccm_version": ([], ctypes.c_char_p),
     }
@@ -227,6 +236,13 @@ def ccm_plan_stage_times(plan: int):
     out = (ctypes.c_double * 4)()
     _check(_lib.ccm_plan_stage_times(plan, out))
     return list(out)
+
+
+def ccm_plan_search_stats(plan: int) -> dict:
+    """Work counts of the last run of a plan made with CCM_SEARCH_STATS."""
+    out = ccm_search_stats()
+    _check(_lib.ccm_plan_search_stats(plan, ctypes.byref(out)))
+    return {name: int(getattr(out, name)) for name, _ in ccm_search_stats._fields_}
 
 
 def ccm_run_plain(plan: int, series, rho, stream=None) -> None:

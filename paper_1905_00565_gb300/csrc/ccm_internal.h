@@ -123,9 +123,26 @@ struct KnnParams {
   int32_t* dbg_nbr;       // optional [sum N_m][E+1]
   float* dbg_xhat;        // optional [sum N_m]
   int32_t* err;
+  unsigned long long* stats;  // optional search counters [kStatCount] (kStat*), nullptr: none
   int32_t persistent;     // 1: CTAs pull items from item_counter; 0: item = blockIdx.x
   int32_t merge_at[kMaxE + 1];  // per E: merge pending candidates once a lane holds this many
   int32_t variant[kMaxE + 1];   // per E: kernel variant (0 narrow, 1 wide); same results
+};
+
+// Search counters, accumulated by the kernels when KnnParams::stats is set (a
+// separately compiled counting variant; the results are the same).
+enum : int {
+  kStatBruteTiles = 0,   // query tiles searched by brute force
+  kStatBruteQueries,     // their valid queries
+  kStatPairsBegun,       // query-library pairs whose distance was begun (lanes x points)
+  kStatPairsFull,        // pairs whose distance was completed over all E coordinates
+  kStatPairsPruned,      // pairs skipped by chunk pruning (lanes x chunk points)
+  kStatCandidates,       // candidates appended to the pending buffers
+  kStatMergeSlots,       // lockstep insertion slots: per warp merge, 32 x its largest pending count
+  kStatTableQueries,     // valid queries answered from a distance indexing table
+  kStatTableEntries,     // table entries loaded (per lane, eight per step)
+  kStatTableFallbacks,   // queries that scanned their library instead
+  kStatCount = 16
 };
 
 // Defaults before tuning: merge trigger (pending candidates per lane) and variant.

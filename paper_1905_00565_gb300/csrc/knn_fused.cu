@@ -40,6 +40,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <initializer_list>
+
 #include "ccm_internal.h"
 
 namespace ccm {
@@ -457,7 +459,7 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   }
 }
 
-template <int E, int V>
+template <int E, int V, bool kStats>
 __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, int tile,
                              unsigned char* smem, RingMeta* meta, int& ring_n) {
   constexpr int K = E + 1;  // the window keeps m itself out, so E+1 slots suffice
@@ -511,9 +513,15 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
 #pragma unroll
   for (int s = 0; s < K; ++s) ku[s] = pack_key(INFINITY, INT_MAX);
   int cnt = 0;
+  // counting variant only: warp-uniform step counts, per-lane candidates
+  uint32_t st_begun = 0, st_full = 0, st_pruned = 0, st_cand = 0, st_slots = 0;
 
   auto merge_all = [&]() {
     const int mx = (int)__reduce_max_sync(kFull, (unsigned)cnt);
+    if (kStats) {
+      st_cand += (uint32_t)cnt;
+      st_slots += (uint32_t)mx;
+    }
     for (int b = 0; b < mx; ++b)
       if (b < cnt) insert_sorted<K>(ku, s_buf[b * kThreads + tid]);
     cnt = 0;
@@ -584,6 +592,10 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
         }
       }
       a_first = kInit;
+      if (kStats) {
+        st_begun += kInit;
+        st_full += kInit;
+      }
     }
 #pragma unroll 1
     for (int a = a_first; a < ntp; a += kStep) {
@@ -604,10 +616,12 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
         const float th_max =
             __uint_as_float(__reduce_max_sync(kFull, (uint32_t)(ku[K - 1] >> 32)));
         if (lb > th_max) {
+          if (kStats) st_pruned += kChunk;
           a += kChunk - kStep;
           continue;
         }
       }
+      if (kStats) st_begun += kStep;
       const u64* cp = s_coord + (size_t)(a >> 1) * EP;
       // Partial sums over the first E1 coordinates are lower bounds of the
       // full FP32 sums (all terms are >= 0 and rounding is monotone), so a
@@ -620,8 +634,10 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
       float d[kStep];
 #pragma unroll
       for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+      if (kStats && (kE1<E, V>) == E) st_full += kStep;
       if (!__any_sync(kFull, min_all(d) <= th)) continue;
       if constexpr ((kE1<E, V>) < E) {
+        if (kStats) st_full += kStep;
 #pragma unroll
         for (int pp = 0; pp < kPairs; ++pp) {
           r[pp] = sqdist2_range<E, (kE1<E, V>), E>(qc, cp + pp * EP, r[pp]);
@@ -647,6 +663,20 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
     }
   }
   merge_all();
+  if (kStats) {
+    const uint32_t cand = __reduce_add_sync(kFull, st_cand);
+    const unsigned vq = __popc(__ballot_sync(kFull, valid));
+    if (lane == 0) {
+      unsigned long long* c = p.stats;
+      atomicAdd(&c[kStatPairsBegun], 32ull * st_begun);
+      atomicAdd(&c[kStatPairsFull], 32ull * st_full);
+      atomicAdd(&c[kStatPairsPruned], 32ull * st_pruned);
+      atomicAdd(&c[kStatCandidates], (unsigned long long)cand);
+      atomicAdd(&c[kStatMergeSlots], 32ull * st_slots);
+      atomicAdd(&c[kStatBruteQueries], (unsigned long long)vq);
+      if (tid == 0) atomicAdd(&c[kStatBruteTiles], 1ull);
+    }
+  }
 
   // Epilogue: the E+1 nearest (the window kept the query itself out of the
   // list), simplex weights, prediction, moments.
@@ -695,7 +725,7 @@ constexpr int kHitRankShift = 20;
 static_assert(kTableMaxNm <= (1 << kHitRankShift), "manifold index must fit below the rank");
 static_assert(kTableMaxR <= (1 << (31 - kHitRankShift)), "rank must fit in the hit word");
 
-template <int E>
+template <int E, bool kStats>
 __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
                                    unsigned char* smem, RingMeta* meta, int& ring_n) {
   const int tid = threadIdx.x;
@@ -738,8 +768,10 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
     auto member = [&](int x) -> uint32_t {
       return bytes ? (uint32_t)map[x] : ((mw[x >> 5] >> (x & 31)) & 1u);
     };
+    uint32_t st_entries = 0;
     for (int g = 0; __any_sync(kFull, found <= E && g < groups); g += 2) {
       const bool w0 = found <= E && g < groups, w1 = found <= E && g + 1 < groups;
+      if (kStats) st_entries += (w0 ? 4u : 0u) + (w1 ? 4u : 0u);
       int x[8];  // ranks 4g .. 4g+7 of this query's row (index 0 when not loaded)
       if (p.table_u16) {
         const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u.table_off + col;
@@ -775,6 +807,16 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
           s_hit[found * kThreads + tid] = ((4 * g + c) << kHitRankShift) | xc;  // rank, index
           ++found;
         }
+      }
+    }
+    if (kStats) {
+      const uint32_t ent = __reduce_add_sync(kFull, st_entries);
+      const unsigned vq = __popc(__ballot_sync(kFull, valid));
+      const unsigned fb = __popc(__ballot_sync(kFull, found <= E));
+      if ((tid & 31) == 0) {
+        atomicAdd(&p.stats[kStatTableEntries], (unsigned long long)ent);
+        atomicAdd(&p.stats[kStatTableQueries], (unsigned long long)vq);
+        atomicAdd(&p.stats[kStatTableFallbacks], (unsigned long long)fb);
       }
     }
     int nb[E + 1];
@@ -826,7 +868,7 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
   }
 }
 
-template <int E>
+template <int E, bool kStats>
 // Four CTAs per SM (64 registers a thread): the table walk waits on L2, and
 // more resident warps hide more of it than the few spilled registers cost.
 __global__ void __launch_bounds__(kThreads, 4) knn_table_kernel(KnnParams p) {
@@ -848,12 +890,12 @@ __global__ void __launch_bounds__(kThreads, 4) knn_table_kernel(KnnParams p) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
       continue;
     }
-    process_table_item<E>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
+    process_table_item<E, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
   }
   if (ring_n > 0) flush_ring(p, reinterpret_cast<const float*>(smem), s_meta, ring_n);
 }
 
-template <int E>
+template <int E, bool kStats>
 __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -874,9 +916,9 @@ __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
       continue;
     }
     if (p.variant[E] == 1)
-      process_tile<E, 1>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
+      process_tile<E, 1, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
     else
-      process_tile<E, 0>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
+      process_tile<E, 0, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
   }
   if (ring_n > 0)
     flush_ring(p, reinterpret_cast<const float*>(smem + kCoordBytes + kBufBytes), s_meta, ring_n);
@@ -900,9 +942,9 @@ cudaError_t knn_table_prepare() {
   // the largest bitmap any plan may need (manifolds up to kTableMaxNm points);
   // set once, so that plans of different sizes never lower it for each other
 #define CCM_TPREP(EV)                                                             \
-  {                                                                               \
+  for (const auto fn : {knn_table_kernel<EV, false>, knn_table_kernel<EV, true>}) { \
     const cudaError_t e = cudaFuncSetAttribute(                                   \
-        knn_table_kernel<EV>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+        fn, cudaFuncAttributeMaxDynamicSharedMemorySize,                          \
         (int)knn_table_smem(kTableMaxNm));                                        \
     if (e != cudaSuccess) return e;                                               \
   }
@@ -912,14 +954,17 @@ cudaError_t knn_table_prepare() {
 }
 
 cudaError_t knn_table_occupancy(int max_nm, int* ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_table_kernel<kMaxE>, kThreads,
-                                                       knn_table_smem(max_nm));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_table_kernel<kMaxE, false>,
+                                                       kThreads, knn_table_smem(max_nm));
 }
 
 cudaError_t launch_knn_table(const KnnParams& p, int E, int max_nm, int grid, cudaStream_t s) {
 #define CCM_TLAUNCH(EV)                                                           \
   if (E == EV) {                                                                  \
-    knn_table_kernel<EV><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p);       \
+    if (p.stats)                                                                  \
+      knn_table_kernel<EV, true><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p); \
+    else                                                                          \
+      knn_table_kernel<EV, false><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p); \
     return cudaGetLastError();                                                    \
   }
   CCM_FOR_E(CCM_TLAUNCH)
@@ -942,7 +987,10 @@ cudaError_t launch_obs(const float* series, const int32_t* order, const ObsJob* 
 cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s) {
 #define CCM_LAUNCH(EV)                                                          \
   if (E == EV) {                                                                \
-    knn_fused_kernel<EV><<<grid, kThreads, kSmemBytes, s>>>(p);                 \
+    if (p.stats)                                                                \
+      knn_fused_kernel<EV, true><<<grid, kThreads, kSmemBytes, s>>>(p);         \
+    else                                                                        \
+      knn_fused_kernel<EV, false><<<grid, kThreads, kSmemBytes, s>>>(p);        \
     return cudaGetLastError();                                                  \
   }
   CCM_FOR_E(CCM_LAUNCH)
@@ -952,9 +1000,9 @@ cudaError_t launch_knn(const KnnParams& p, int E, int grid, cudaStream_t s) {
 
 cudaError_t knn_prepare() {
 #define CCM_PREP(EV)                                                            \
-  {                                                                             \
+  for (const auto fn : {knn_fused_kernel<EV, false>, knn_fused_kernel<EV, true>}) { \
     const cudaError_t e = cudaFuncSetAttribute(                                 \
-        knn_fused_kernel<EV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes); \
+        fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);           \
     if (e != cudaSuccess) return e;                                             \
   }
   CCM_FOR_E(CCM_PREP)
@@ -965,8 +1013,8 @@ cudaError_t knn_prepare() {
 cudaError_t knn_occupancy(int E, int* ctas) {
 #define CCM_OCC(EV)                                                             \
   if (E == EV)                                                                  \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_fused_kernel<EV>, kThreads, \
-                                                         kSmemBytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_fused_kernel<EV, false>,   \
+                                                         kThreads, kSmemBytes);
   CCM_FOR_E(CCM_OCC)
 #undef CCM_OCC
   return cudaErrorInvalidValue;

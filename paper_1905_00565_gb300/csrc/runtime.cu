@@ -94,7 +94,7 @@ ccm_status copy_problem(const ccm_problem* p, ProblemCopy* pc) {
   pc->seed = p->seed;
   pc->flags = p->flags;
   if (p->flags & ~(uint32_t)(CCM_INPUT_ON_DEVICE | CCM_OUTPUT_ON_DEVICE | CCM_NO_AUTOTUNE |
-                             CCM_NO_TABLE))
+                             CCM_NO_TABLE | CCM_SEARCH_STATS))
     return fail(CCM_EINVAL, "unknown flag bits");
   pc->theiler = p->theiler;
   pc->weight_floor = p->weight_floor;
@@ -174,6 +174,7 @@ struct UnitList {
     return g;
   }
   double brute_flops = 0.0;           // 3E per pair of the units searched by brute force
+  double brute_pairs = 0.0;           // query-library pairs of those units
   int table_u16() const { return max_nm < 65536 ? 1 : 0; }
   size_t table_elem() const { return table_u16() ? 2 : 4; }
   int64_t n_rho = 0, q_total = 0, nbr_total = 0, lib_dbg_total = 0;  // per output realization
@@ -397,7 +398,10 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
                                         (double)u.n_targets * nq * 64.0);
               }
             }
-            if (u.table_R == 0) ul->brute_flops += 3.0 * E * (double)u.n_m * (double)L;
+            if (u.table_R == 0) {
+              ul->brute_flops += 3.0 * E * (double)u.n_m * (double)L;
+              ul->brute_pairs += (double)u.n_m * (double)L;
+            }
             ul->lib_total += L;
             ul->part_total += (int64_t)u.n_tiles * u.n_targets;
             ul->emin = std::min(ul->emin, E);
@@ -478,7 +482,8 @@ void sort_items(UnitList* ul) {
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
          counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
-         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_d2 = 0, total = 0;
+         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_d2 = 0, stats = 0,
+         total = 0;
 };
 
 Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t scratch_floats) {
@@ -509,6 +514,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.items_table = take(sizeof(WorkItem) * ul.items_table.size());
   a.obs = take(sizeof(double) * kObsStride * (size_t)ul.obs_total);
   a.obs_jobs = take(sizeof(ObsJob) * ul.obs_jobs.size());
+  a.stats = take(sizeof(unsigned long long) * kStatCount);
   a.total = o;
   return a;
 }
@@ -695,7 +701,8 @@ cudaError_t enqueue_obs(char* base, const Arena& ar, const UnitList& ul, cudaStr
 ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const Tuning& tn,
                          int grid, int grid_table, int persistent, int32_t* dbg_lib,
                          int32_t* dbg_nbr, float* dbg_xhat, cudaStream_t s,
-                         cudaEvent_t* ev = nullptr, bool capturing = false) {
+                         cudaEvent_t* ev = nullptr, bool capturing = false,
+                         bool stats = false) {
   // Inside stream capture an event record becomes a graph node only with the
   // external flag; outside capture the plain record is the valid form.
   auto record = [&](cudaEvent_t e) {
@@ -705,6 +712,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
   CCM_CUDA(cudaMemsetAsync(base + ar.err, 0, sizeof(int32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.counter, 0, 2 * (kMaxE + 1) * sizeof(uint32_t), s));
   CCM_CUDA(cudaMemsetAsync(base + ar.done, 0, sizeof(uint32_t) * ul.units.size(), s));
+  if (stats) CCM_CUDA(cudaMemsetAsync(base + ar.stats, 0, sizeof(unsigned long long) * kStatCount, s));
   if (ev) CCM_CUDA(record(ev[0]));
   CCM_CUDA(launch_order(reinterpret_cast<const float*>(base + ar.series),
                         reinterpret_cast<const OrderJob*>(base + ar.orders),
@@ -736,6 +744,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
   KnnParams kp = knn_params(base, ar, ul, persistent, tn);
   kp.dbg_nbr = dbg_nbr;
   kp.dbg_xhat = dbg_xhat;
+  if (stats) kp.stats = reinterpret_cast<unsigned long long*>(base + ar.stats);
   // One launch per E (a kernel specialised for one E keeps its registers for
   // that E); each drains its own queue, larger items first, so the launches
   // follow each other with short tails.
@@ -1017,6 +1026,7 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.pair_count = pl->ul.pairs;
   in.flop_count = pl->ul.flops;
   in.brute_flop_count = pl->ul.brute_flops;
+  in.brute_pair_count = pl->ul.brute_pairs;
   in.table_bytes = (pl->ul.table_elem() + sizeof(float)) * (size_t)pl->ul.table_total;
   // launches of one ccm_run: order, tables, sampler, one brute-force and one
   // table-scan kernel per E present
@@ -1084,7 +1094,7 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
                       : nullptr;
     ccm_status st =
         enqueue_sweep(base, plan->ar, ul, plan->tuning, plan->grid, plan->grid_table, 1, d_lib,
-                      d_nbr, d_xh, s, plan->ev);
+                      d_nbr, d_xh, s, plan->ev, false, (pc.flags & CCM_SEARCH_STATS) != 0);
     if (st != CCM_OK) return st;
     if (!out_dev) {
       if (dbg->libraries) CCM_CUDA(cudaMemcpyAsync(dbg->libraries, d_lib, lb, cudaMemcpyDeviceToHost, s));
@@ -1108,7 +1118,7 @@ ccm_status ccm_run_ex(ccm_plan_t* plan, const float* series, double* rho, const 
       CCM_CUDA(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
       ccm_status st = enqueue_sweep(base, plan->ar, plan->ul, plan->tuning, plan->grid,
                                     plan->grid_table, 1, nullptr, nullptr, nullptr, plan->stream,
-                                    plan->ev, true);
+                                    plan->ev, true, (pc.flags & CCM_SEARCH_STATS) != 0);
       const cudaError_t ce = cudaStreamEndCapture(plan->stream, &graph);
       if (st != CCM_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -1145,6 +1155,26 @@ ccm_status ccm_plan_stage_times(const ccm_plan_t* plan, double* stage_ms) {
     CCM_CUDA(cudaEventElapsedTime(&t, plan->ev[q], plan->ev[q + 1]));
     stage_ms[q] = t;
   }
+  return CCM_OK;
+}
+
+ccm_status ccm_plan_search_stats(const ccm_plan_t* plan, ccm_search_stats* out) {
+  if (!plan || !out) return fail(CCM_EINVAL, "NULL argument");
+  if (!(plan->pc.flags & CCM_SEARCH_STATS))
+    return fail(CCM_EINVAL, "the plan was made without CCM_SEARCH_STATS");
+  CCM_CUDA(cudaSetDevice(plan->ctx->device));
+  unsigned long long c[kStatCount];
+  CCM_CUDA(cudaMemcpy(c, plan->d_arena + plan->ar.stats, sizeof(c), cudaMemcpyDeviceToHost));
+  out->brute_tiles = c[kStatBruteTiles];
+  out->brute_queries = c[kStatBruteQueries];
+  out->pairs_begun = c[kStatPairsBegun];
+  out->pairs_full = c[kStatPairsFull];
+  out->pairs_pruned = c[kStatPairsPruned];
+  out->candidates = c[kStatCandidates];
+  out->merge_slots = c[kStatMergeSlots];
+  out->table_queries = c[kStatTableQueries];
+  out->table_entries = c[kStatTableEntries];
+  out->table_fallbacks = c[kStatTableFallbacks];
   return CCM_OK;
 }
 
