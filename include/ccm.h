@@ -225,7 +225,13 @@ ccm_status ccm_run_plain(ccm_plan_t* plan, const float* series, double* rho, voi
  * so the caller may free it on return).  The serving thread admits queued
  * jobs while their device footprints fit the free budget, batches admitted
  * jobs' work items into shared persistent launches, and overlaps them on
- * several streams.  CCM_ETOOLARGE if the footprint exceeds the whole budget. */
+ * several streams.  CCM_ETOOLARGE if the footprint exceeds the whole budget.
+ * A batch whose launch fails (a CUDA call returns an error) fails its own jobs
+ * with CCM_ECUDA at ccm_poll; the other jobs and later batches are unaffected.
+ * Test hook: the environment variable CCM_FAULT_INJECT_BATCH=n, read by
+ * ccm_context_create, makes the launch of that context's batch n (0-based, in
+ * launch order) fail on the host as if a CUDA call had failed after its
+ * uploads were enqueued; no device work is faulted. */
 ccm_status ccm_submit(ccm_context* ctx, const ccm_problem* prob, const float* series,
                       uint64_t* ticket);
 

@@ -62,11 +62,14 @@ struct ObsJob {
 // (zero past the tile's end), then mean(x) and sum of (x_q - mean(x))^2.
 constexpr int kObsStride = 264;        // doubles per record (64-byte multiple)
 
-// One work item of the fused kernel: a query tile of a unit.
+// One work item of the fused kernels: query tiles [tile, tile + chunk) of a
+// unit (chunk = kBruteChunk for the brute-force kernel, kTableChunk for the
+// table kernel; the last item of a unit may hold fewer tiles).
 struct WorkItem {
   int32_t unit;
   int32_t tile;
 };
+constexpr int kBruteChunk = 8;         // query tiles per brute-force work item (one staging)
 
 // Query order job: one per (job, library variable, E, tau).
 struct OrderJob {
@@ -146,7 +149,7 @@ enum : int {
 };
 
 // Defaults before tuning: merge trigger (pending candidates per lane) and variant.
-constexpr int kDefaultMergeAt = 9;
+constexpr int kDefaultMergeAt = 4;
 constexpr int kDefaultVariant = 1;
 
 // Error flag values written by kernels.

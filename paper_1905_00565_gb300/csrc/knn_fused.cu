@@ -9,26 +9,26 @@
 // realization into the Pearson skill (Sect. 2.1).
 //
 // Design (GB300, FP32 on the CUDA cores; E <= 10 is not a dense contraction):
-//  * persistent CTAs pull (realization, query tile) items, sorted by cost,
-//    from an atomic counter;
+//  * persistent CTAs pull work items, sorted by cost, from an atomic counter;
+//    a brute-force item is up to eight query tiles of one realization, so a
+//    library that fits one shared-memory tile is staged once for all of them;
 //  * each thread owns one query; library points sit in shared memory in
 //    pairs, packed {a_e, b_e} per coordinate, so one sub.f32x2 + fma.f32x2
 //    pair advances the query's distances to two points;
-//  * the library is staged through shared memory tile by tile; a broadcast
-//    128-bit load feeds the packed operations directly;
+//  * a broadcast 128-bit load feeds the packed operations directly;
 //  * squared distances are accumulated in coordinate order (first term a
 //    rounded product, then one fused multiply-add per coordinate), the same
 //    rounding sequence the FP32 selection is defined by;
-//  * each query keeps its E+1 best (squared distance, index) in registers,
-//    sorted; candidates under the current threshold (and outside the
-//    exclusion window, which always holds the query itself) are appended to
-//    a small per-query buffer in shared memory and merged, warp-wide, when a
-//    buffer runs full, so a rare insertion in one lane does not stall the
-//    warp for a full sorted insertion every time;
-//  * the library is visited in query order from the run nearest the tile
-//    (wrapping around), so candidates are compared by the packed key
-//    (squared distance, index): equal distances keep index order whatever
-//    the visiting order;
+//  * the library is visited in query order from the run nearest each warp's
+//    queries (wrapping around); 16-point chunks whose bounding box lies
+//    farther than every lane's threshold are skipped whole;
+//  * selection: each query keeps the K = E+1 smallest distances seen as a
+//    sorted float list in registers (a min/max network, no index
+//    bookkeeping), which is its running threshold, and the (squared
+//    distance, index) keys of every candidate at or below the threshold in
+//    its column of a shared-memory buffer; the column is compacted when it
+//    runs full and sorted at the end, so the E+1 nearest come out in
+//    (distance, index) order however the library was visited;
 //  * the epilogue forms u_i = exp(-d_i/d_1) (optionally floored), the
 //    prediction, and the FP64 moments of each (tile, target): predictions go
 //    to a shared-memory ring whose eight slots are reduced by eight warps at
@@ -52,10 +52,10 @@ using u64 = unsigned long long;
 constexpr int kThreads = 256;             // threads per CTA = queries per tile
 constexpr int kQT = kThreads;             // queries per tile (one per thread)
 static_assert((kQT & (kQT - 1)) == 0, "tile moments rely on a power-of-two tile");
-constexpr int kBuf = 16;                  // pending candidates per query
-constexpr int kCoordBytes = 32 * 1024;    // shared memory for one library tile + chunk boxes
-constexpr int kBoxBytes = 2 * 1024;       // chunk bounding boxes, at the end of that region
-constexpr int kChunk = 32;                // library points per bounding box
+constexpr int kBuf = 20;                  // candidate keys per query (a column of the buffer)
+constexpr int kCoordBytes = 24 * 1024;    // shared memory for one library tile + chunk boxes
+constexpr int kBoxBytes = 4 * 1024;       // chunk bounding boxes, at the end of that region
+constexpr int kChunk = 16;                // library points per bounding box
 constexpr int kBufBytes = kBuf * kThreads * 8;
 // Predictions staged for their FP64 moments: kRing (tile, target) vectors of
 // kQT floats, reduced together, one warp each, when the ring is full.
@@ -85,7 +85,7 @@ struct TileShape {
   static constexpr int D = E < 3 ? E : 3;                       // coordinates a chunk box bounds
   // library points per tile: a point pair takes EP*8 bytes of coordinates + 8 of indices
   static constexpr int LT = ((kCoordBytes - kBoxBytes) / (EP * 8 + 8)) * 2 / 64 * 64;
-  static_assert(LT >= 64 && LT % kChunk == 0, "tile must hold whole chunks");
+  static_assert(LT >= 64 && LT % 32 == 0, "tile must hold whole warps of chunks");
   static_assert((LT / kChunk) * 2 * D * 4 <= kBoxBytes, "chunk boxes must fit");
 };
 
@@ -459,8 +459,110 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   }
 }
 
+// Stage library points [t0, t0 + nt) of a unit's library (query order) into
+// shared memory: coordinates in packed pairs, indices, and the bounding box
+// of every kChunk consecutive points over the first D coordinates.  The tile
+// is padded to whole chunks with sentinel points (infinite coordinates, index
+// INT_MAX) that are never selected.  Block-wide; the caller brackets it with
+// barriers.
+template <int E>
+__device__ __noinline__ void stage_library(const float* sj, const int32_t* lib, int off, int tau,
+                                              int t0, int nt, u64* s_coord, int32_t* s_lidx,
+                                              float* s_box) {
+  constexpr int EP = TileShape<E>::EP;
+  constexpr int D = TileShape<E>::D;
+  const int tid = threadIdx.x;
+  const int ntp = (nt + kChunk - 1) / kChunk * kChunk;
+  for (int a = tid; a < (ntp + 31) / 32 * 32; a += kThreads) {  // whole warps: the box shuffles
+    const int pp = a >> 1, half = a & 1;
+    float c0[D];
+    if (a < nt) {
+      const int l = lib[t0 + a];
+      s_lidx[a] = l;
+      float* cpair = reinterpret_cast<float*>(s_coord + (size_t)pp * EP);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const float c = sj[l + off - e * tau];
+        cpair[2 * e + half] = c;
+        if (e < D) c0[e] = c;
+      }
+      if (EP > E) cpair[2 * E + half] = 0.f;
+    } else {
+      if (a < ntp) {  // sentinel point: infinite distance, never selected
+        s_lidx[a] = INT_MAX;
+        float* cpair = reinterpret_cast<float*>(s_coord + (size_t)pp * EP);
+#pragma unroll
+        for (int e = 0; e < E; ++e) cpair[2 * e + half] = INFINITY;
+        if (EP > E) cpair[2 * E + half] = 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < D; ++e) c0[e] = INFINITY;
+    }
+    // chunk boxes over the first D coordinates: one per half-warp (sentinels
+    // widen only hi)
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      float lo = c0[e], hi = c0[e];
+#pragma unroll
+      for (int o = kChunk / 2; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+      }
+      if ((a & (kChunk - 1)) == 0 && a < ntp) {
+        s_box[(a / kChunk) * 2 * D + e] = lo;
+        s_box[(a / kChunk) * 2 * D + D + e] = hi;
+      }
+    }
+  }
+}
+
+// The running threshold: t[0..K) holds the K smallest squared distances (as
+// values, ties repeated) of the candidates seen so far, ascending.  Inserting
+// x is a min/max network: slot s becomes min(t[s], max(t[s-1], x)), which
+// leaves the list unchanged when x is not below t[K-1].
+template <int K>
+__device__ __forceinline__ void thresh_insert(float (&t)[K], float x) {
+#pragma unroll
+  for (int s = K - 1; s > 0; --s) t[s] = fminf(t[s], fmaxf(t[s - 1], x));
+  t[0] = fminf(t[0], x);
+}
+
+// Ascending insertion sort of one thread's candidate column (n keys, stride
+// kThreads) in shared memory.
+__device__ __forceinline__ void sort_column(u64* col, int n) {
+  for (int i = 1; i < n; ++i) {
+    const u64 x = col[i * kThreads];
+    int j = i - 1;
+    for (; j >= 0; --j) {
+      const u64 y = col[j * kThreads];
+      if (y <= x) break;
+      col[(j + 1) * kThreads] = y;
+    }
+    col[(j + 1) * kThreads] = x;
+  }
+}
+
+// Brute-force search of one work item: query tiles [tile0, tile0 +
+// kBruteChunk) of a unit.  When the whole library fits one shared-memory tile
+// it is staged once for all of them; each warp starts its scan at the library
+// run nearest its own 32 queries (the library is in query order) and wraps
+// around.  Larger libraries are staged tile by tile for every query tile.
+//
+// Selection.  Each query keeps (a) the running threshold t[] of the K = E+1
+// smallest squared distances seen (registers, min/max network) and (b) a
+// column of the candidate buffer in shared memory with the keys (squared
+// distance, index) of every candidate whose distance was at most the threshold
+// when it was seen.  Every key that can still be among the final K smallest
+// is in the column: a dropped key had a distance above a threshold that is
+// itself at least the final K-th smallest value.  The threshold is brought up
+// to date warp-wide once some lane has merge_at new candidates (the network is
+// cheap: no index bookkeeping); a nearly full column is compacted to the keys
+// at or below the threshold, and, if ties still leave it full, sorted and cut
+// to the K smallest keys.  At the end the column is compacted and sorted: its
+// first K keys are the E+1 nearest neighbours in (distance, index) order,
+// exactly the list the sorted insertion of every candidate would give.
 template <int E, int V, bool kStats>
-__device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, int tile,
+__device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
                              unsigned char* smem, RingMeta* meta, int& ring_n) {
   constexpr int K = E + 1;  // the window keeps m itself out, so E+1 slots suffice
   constexpr int EP = TileShape<E>::EP;
@@ -468,11 +570,11 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   constexpr int D = TileShape<E>::D;
   u64* s_coord = reinterpret_cast<u64*>(smem);                                   // [LT/2][EP]
   int32_t* s_lidx = reinterpret_cast<int32_t*>(smem + (size_t)(LT / 2) * EP * 8);  // [LT]
-  float* s_box = reinterpret_cast<float*>(smem + kCoordBytes - kBoxBytes);       // [LT/32][2D]
+  float* s_box = reinterpret_cast<float*>(smem + kCoordBytes - kBoxBytes);       // [LT/kChunk][2D]
   u64* s_buf = reinterpret_cast<u64*>(smem + kCoordBytes);                      // [kBuf][kThreads]
   float* s_ring = reinterpret_cast<float*>(smem + kCoordBytes + kBufBytes);      // [kRing][kQT]
 
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n_m = u.n_m, L = u.L, tau = u.tau, W = u.theiler;
   const int off = (E - 1) * tau;
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
@@ -480,218 +582,232 @@ __device__ void process_tile(const KnnParams& p, const UnitDesc& u, int unit, in
   const int32_t* order = p.order + u.order_off;
   constexpr int kStep = kStepE<E, V>;
   constexpr int kPairs = kStep / 2;
-  // merge trigger: at most kBuf - kStep + 1 so that a step can always append
-  const int merge_at = max(1, min(p.merge_at[E], kBuf - kStep + 1));
-  // the first kInit points of the order go straight into the empty list
+  constexpr int kRoom = kBuf - kStep;   // a column above this cannot take another step
+  static_assert(K + kStep <= kBuf, "a cut column must leave room for a step");
+  const int merge_at = max(1, min(p.merge_at[E], kRoom));
+  // the first kInit points of a query's scan go straight into its threshold
   constexpr int kInit = (K + kStep - 1) / kStep * kStep;
+  static_assert(kInit <= kChunk, "the initial points lie in the first chunk");
+  u64* col = s_buf + tid;  // this thread's candidate column
 
-  // A warp's 32 queries are consecutive positions of the query order.
-  const int pos = tile * kQT + tid;
-  const bool valid = pos < n_m;
-  const int m = order[valid ? pos : n_m - 1];
-  u64 qc[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const float c = sj[m + off - e * tau];
-    qc[e] = pack2(c, c);
-  }
-  // Bounding box of the warp's queries over the first D coordinates.
-  float qlo[D], qhi[D];
-#pragma unroll
-  for (int e = 0; e < D; ++e) {
-    float lo = sj[m + off - e * tau], hi = lo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
-      hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
-    }
-    qlo[e] = lo;
-    qhi[e] = hi;
-  }
-
-  u64 ku[K];  // the E+1 smallest keys so far, ascending
-#pragma unroll
-  for (int s = 0; s < K; ++s) ku[s] = pack_key(INFINITY, INT_MAX);
-  int cnt = 0;
-  // counting variant only: warp-uniform step counts, per-lane candidates
-  uint32_t st_begun = 0, st_full = 0, st_pruned = 0, st_cand = 0, st_slots = 0;
-
-  auto merge_all = [&]() {
-    const int mx = (int)__reduce_max_sync(kFull, (unsigned)cnt);
-    if (kStats) {
-      st_cand += (uint32_t)cnt;
-      st_slots += (uint32_t)mx;
-    }
-    for (int b = 0; b < mx; ++b)
-      if (b < cnt) insert_sorted<K>(ku, s_buf[b * kThreads + tid]);
-    cnt = 0;
-  };
-
-  // The library is stored in query order, so a run of it sits near this
-  // tile's queries: start there (wrapping around) so that the thresholds are
-  // tight from the first chunks on.
-  const int a0 = (int)((int64_t)L * (int64_t)(tile * kQT) / n_m);
-  for (int t0 = 0; t0 < L; t0 += LT) {
-    const int nt = min(LT, L - t0);
-    const int ntp = (nt + kChunk - 1) / kChunk * kChunk;
-    __syncthreads();  // the previous tile has been consumed
-    for (int a = tid; a < ntp; a += kThreads) {  // a warp stages one chunk
-      const int pp = a >> 1, half = a & 1;
-      float* cpair = reinterpret_cast<float*>(s_coord + (size_t)pp * EP);
-      float c0[D];
-      if (a < nt) {
-        int g = a0 + t0 + a;
-        g -= (g >= L) ? L : 0;
-        const int l = lib[g];
-        s_lidx[a] = l;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const float c = sj[l + off - e * tau];
-          cpair[2 * e + half] = c;
-          if (e < D) c0[e] = c;
-        }
-      } else {  // sentinel point: infinite distance, never selected
-        s_lidx[a] = INT_MAX;
-#pragma unroll
-        for (int e = 0; e < E; ++e) cpair[2 * e + half] = INFINITY;
-#pragma unroll
-        for (int e = 0; e < D; ++e) c0[e] = INFINITY;
-      }
-      if (EP > E) cpair[2 * E + half] = 0.f;
-      // chunk box over the first D coordinates (sentinels widen only hi)
-#pragma unroll
-      for (int e = 0; e < D; ++e) {
-        float lo = c0[e], hi = c0[e];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
-          hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
-        }
-        if (lane == 0) {
-          s_box[(a >> 5) * 2 * D + e] = lo;
-          s_box[(a >> 5) * 2 * D + D + e] = hi;
-        }
-      }
-    }
+  const bool single = L <= LT;
+  const int tile1 = min(u.n_tiles, tile0 + kBruteChunk);
+  if (single) {
+    __syncthreads();  // the previous item's readers of the tile are done
+    stage_library<E>(sj, lib, off, tau, 0, L, s_coord, s_lidx, s_box);
     __syncthreads();
-
-    int a_first = 0;
-    if (t0 == 0) {
-      // The first kInit points (near this tile: the scan starts there) fill
-      // the list directly, each inserted into a list of known length; the
-      // threshold is then finite before the first candidate is appended.
+  }
+  for (int tile = tile0; tile < tile1; ++tile) {
+    // A warp's 32 queries are consecutive positions of the query order.
+    const int pos = tile * kQT + tid;
+    const bool valid = pos < n_m;
+    const int m = order[valid ? pos : n_m - 1];
+    u64 qc[E];
 #pragma unroll
-      for (int pp = 0; pp < kInit / 2; ++pp) {
-        float d2[2];
-        unpack2(sqdist2_range<E, 0, E>(qc, s_coord + (size_t)pp * EP, 0ull), d2[0], d2[1]);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int l = s_lidx[2 * pp + h];
-          const u64 key = (abs(l - m) > W) ? pack_key(d2[h], l) : pack_key(INFINITY, INT_MAX);
-          insert_prefix<K>(ku, key, 2 * pp + h);
-        }
-      }
-      a_first = kInit;
-      if (kStats) {
-        st_begun += kInit;
-        st_full += kInit;
-      }
+    for (int e = 0; e < E; ++e) {
+      const float c = sj[m + off - e * tau];
+      qc[e] = pack2(c, c);
     }
-#pragma unroll 1
-    for (int a = a_first; a < ntp; a += kStep) {
-      if ((a & (kChunk - 1)) == 0) {
-        // Chunk pruning.  gap_e = max(0, lo_e - qhi_e, qlo_e - hi_e) bounds
-        // |q_e - x_e| from below for every query q of the warp and point x of
-        // the chunk, in FP32 too (rounding is monotone); summed in the
-        // distance's own order over the first D coordinates it bounds every
-        // FP32 squared distance between them from below.  A chunk whose bound
-        // exceeds every lane's threshold holds no candidate.
-        const float* bx = s_box + (a >> 5) * 2 * D;
-        float lb = 0.f;
+    // Bounding box of the warp's queries over the first D coordinates.
+    float qlo[D], qhi[D];
 #pragma unroll
-        for (int e = 0; e < D; ++e) {
-          const float g = fmaxf(fmaxf(__fsub_rn(bx[e], qhi[e]), __fsub_rn(qlo[e], bx[D + e])), 0.f);
-          lb = (e == 0) ? __fmul_rn(g, g) : __fmaf_rn(g, g, lb);
-        }
-        const float th_max =
-            __uint_as_float(__reduce_max_sync(kFull, (uint32_t)(ku[K - 1] >> 32)));
-        if (lb > th_max) {
-          if (kStats) st_pruned += kChunk;
-          a += kChunk - kStep;
-          continue;
+    for (int e = 0; e < D; ++e) {
+      float lo = sj[m + off - e * tau], hi = lo;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+      }
+      qlo[e] = lo;
+      qhi[e] = hi;
+    }
+    // the library position nearest this warp's queries (in query order)
+    const int aw = (int)((int64_t)L * (int64_t)(tile * kQT + warp * 32) / n_m);
+
+    float tl[K];  // running threshold: the K smallest distances so far, ascending
+#pragma unroll
+    for (int s = 0; s < K; ++s) tl[s] = INFINITY;
+    int cnt = 0, done = 0;  // keys in the column; of them, already in tl
+    // counting variant only: warp-uniform step counts, per-lane candidates
+    uint32_t st_begun = 0, st_full = 0, st_pruned = 0, st_cand = 0, st_slots = 0;
+
+    // bring tl up to date with the column's new keys (lockstep over the lanes)
+    auto update = [&]() {
+      const int mx = (int)__reduce_max_sync(kFull, (unsigned)(cnt - done));
+      if (kStats) {
+        st_cand += (uint32_t)(cnt - done);
+        st_slots += (uint32_t)mx;
+      }
+      for (int b = 0; b < mx; ++b)
+        if (b < cnt - done) thresh_insert<K>(tl, key_dist(col[(done + b) * kThreads]));
+      done = cnt;
+    };
+    // keep the keys at or below the threshold (in order)
+    auto compact = [&]() {
+      const float th = tl[K - 1];
+      const int mx = (int)__reduce_max_sync(kFull, (unsigned)cnt);
+      int w = 0;
+      for (int b = 0; b < mx; ++b) {
+        if (b < cnt) {
+          const u64 x = col[b * kThreads];
+          if (key_dist(x) <= th) col[(w++) * kThreads] = x;
         }
       }
-      if (kStats) st_begun += kStep;
-      const u64* cp = s_coord + (size_t)(a >> 1) * EP;
-      // Partial sums over the first E1 coordinates are lower bounds of the
-      // full FP32 sums (all terms are >= 0 and rounding is monotone), so a
-      // step whose partials are all above every lane's threshold cannot
-      // contribute a candidate and skips the remaining coordinates.
-      u64 r[kPairs];
-#pragma unroll
-      for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, (kE1<E, V>)>(qc, cp + pp * EP, 0ull);
-      const float th = key_dist(ku[K - 1]);
-      float d[kStep];
-#pragma unroll
-      for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
-      if (kStats && (kE1<E, V>) == E) st_full += kStep;
-      if (!__any_sync(kFull, min_all(d) <= th)) continue;
-      if constexpr ((kE1<E, V>) < E) {
-        if (kStats) st_full += kStep;
-#pragma unroll
-        for (int pp = 0; pp < kPairs; ++pp) {
-          r[pp] = sqdist2_range<E, (kE1<E, V>), E>(qc, cp + pp * EP, r[pp]);
-          unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+      cnt = done = w;
+    };
+    auto make_room = [&]() {
+      update();
+      if (__any_sync(kFull, cnt > kRoom)) compact();
+      if (__any_sync(kFull, cnt > kRoom)) {  // ties at the threshold: keep the K smallest keys
+        if (cnt > kRoom) {
+          sort_column(col, cnt);
+          cnt = done = K;
         }
-        if (!__any_sync(kFull, min_all(d) <= th)) continue;
       }
-      const u64 thk = ku[K - 1];
+    };
+
+    // Scan the staged points [0, nt) from position `base` (a chunk start),
+    // wrapping around; `first`: the scan's first kInit points fill tl.
+    auto scan = [&](int nt, int base, bool first) {
+      const int ntp = (nt + kChunk - 1) / kChunk * kChunk;
+      int i = 0;
+      if (first) {
 #pragma unroll
-      for (int pt = 0; pt < kStep; ++pt) {
-        if (d[pt] <= th) {
-          const int l = s_lidx[a + pt];
-          const u64 key = pack_key(d[pt], l);
-          // below the current last entry, outside the exclusion window
-          // (W = 0 drops only m itself)
-          if (key < thk && abs(l - m) > W) {
-            s_buf[cnt * kThreads + tid] = key;
-            ++cnt;
+        for (int pp = 0; pp < kInit / 2; ++pp) {
+          int a = base + 2 * pp;
+          a -= (a >= ntp) ? ntp : 0;
+          float d2[2];
+          unpack2(sqdist2_range<E, 0, E>(qc, s_coord + (size_t)(a >> 1) * EP, 0ull), d2[0], d2[1]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int l = s_lidx[a + h];
+            if (l != INT_MAX && abs(l - m) > W) {
+              thresh_insert<K>(tl, d2[h]);
+              col[(cnt++) * kThreads] = pack_key(d2[h], l);
+            }
           }
         }
+        done = cnt;
+        if (kStats) {
+          st_begun += kInit;
+          st_full += kInit;
+        }
+        if (__any_sync(kFull, cnt > kRoom)) make_room();
+        i = kInit;
       }
-      if (__any_sync(kFull, cnt >= merge_at)) merge_all();
-    }
-  }
-  merge_all();
-  if (kStats) {
-    const uint32_t cand = __reduce_add_sync(kFull, st_cand);
-    const unsigned vq = __popc(__ballot_sync(kFull, valid));
-    if (lane == 0) {
-      unsigned long long* c = p.stats;
-      atomicAdd(&c[kStatPairsBegun], 32ull * st_begun);
-      atomicAdd(&c[kStatPairsFull], 32ull * st_full);
-      atomicAdd(&c[kStatPairsPruned], 32ull * st_pruned);
-      atomicAdd(&c[kStatCandidates], (unsigned long long)cand);
-      atomicAdd(&c[kStatMergeSlots], 32ull * st_slots);
-      atomicAdd(&c[kStatBruteQueries], (unsigned long long)vq);
-      if (tid == 0) atomicAdd(&c[kStatBruteTiles], 1ull);
-    }
-  }
-
-  // Epilogue: the E+1 nearest (the window kept the query itself out of the
-  // list), simplex weights, prediction, moments.
-  float dd[E + 1];
-  int nb[E + 1];
+#pragma unroll 1
+      for (; i < ntp; i += kStep) {
+        int a = base + i;
+        a -= (a >= ntp) ? ntp : 0;
+        if ((a & (kChunk - 1)) == 0) {
+          // Chunk pruning.  gap_e = max(0, lo_e - qhi_e, qlo_e - hi_e) bounds
+          // |q_e - x_e| from below for every query q of the warp and point x of
+          // the chunk, in FP32 too (rounding is monotone); summed in the
+          // distance's own order over the first D coordinates it bounds every
+          // FP32 squared distance between them from below.  A chunk whose bound
+          // exceeds every lane's threshold holds no candidate.
+          const float* bx = s_box + (a / kChunk) * 2 * D;
+          float lb = 0.f;
 #pragma unroll
-  for (int s = 0; s <= E; ++s) {
-    dd[s] = key_dist(ku[s]);
-    nb[s] = key_index(ku[s]);
+          for (int e = 0; e < D; ++e) {
+            const float g = fmaxf(fmaxf(__fsub_rn(bx[e], qhi[e]), __fsub_rn(qlo[e], bx[D + e])), 0.f);
+            lb = (e == 0) ? __fmul_rn(g, g) : __fmaf_rn(g, g, lb);
+          }
+          const float th_max = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(tl[K - 1])));
+          if (lb > th_max) {
+            if (kStats) st_pruned += kChunk;
+            i += kChunk - kStep;
+            continue;
+          }
+        }
+        if (kStats) st_begun += kStep;
+        const u64* cp = s_coord + (size_t)(a >> 1) * EP;
+        // Partial sums over the first E1 coordinates are lower bounds of the
+        // full FP32 sums (all terms are >= 0 and rounding is monotone), so a
+        // step whose partials are all above every lane's threshold cannot
+        // contribute a candidate and skips the remaining coordinates.
+        u64 r[kPairs];
+#pragma unroll
+        for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, (kE1<E, V>)>(qc, cp + pp * EP, 0ull);
+        const float th = tl[K - 1];
+        float d[kStep];
+#pragma unroll
+        for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+        if (kStats && (kE1<E, V>) == E) st_full += kStep;
+        if (!__any_sync(kFull, min_all(d) <= th)) continue;
+        if constexpr ((kE1<E, V>) < E) {
+          if (kStats) st_full += kStep;
+#pragma unroll
+          for (int pp = 0; pp < kPairs; ++pp) {
+            r[pp] = sqdist2_range<E, (kE1<E, V>), E>(qc, cp + pp * EP, r[pp]);
+            unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+          }
+          if (!__any_sync(kFull, min_all(d) <= th)) continue;
+        }
+#pragma unroll
+        for (int pt = 0; pt < kStep; ++pt) {
+          if (d[pt] <= th) {
+            const int l = s_lidx[a + pt];
+            // a real point outside the exclusion window (W = 0 drops only m)
+            if (l != INT_MAX && abs(l - m) > W) col[(cnt++) * kThreads] = pack_key(d[pt], l);
+          }
+        }
+        if (__any_sync(kFull, cnt - done >= merge_at || cnt > kRoom)) make_room();
+      }
+    };
+
+    // The library is staged tile by tile unless it fits one shared-memory tile
+    // (staged once per item above); the first library tile visited is the one
+    // nearest this query tile (the same order in every warp: the staging is
+    // block-wide).
+    const int ntiles = single ? 1 : (L + LT - 1) / LT;
+    const int first_t = single ? 0 : (int)((int64_t)L * (int64_t)(tile * kQT) / n_m) / LT;
+    for (int c = 0; c < ntiles; ++c) {
+      int ti = first_t + c;
+      ti -= (ti >= ntiles) ? ntiles : 0;
+      const int t0 = ti * LT, nt = min(LT, L - t0);
+      if (!single) {
+        __syncthreads();  // the previous library tile has been consumed
+        stage_library<E>(sj, lib, off, tau, t0, nt, s_coord, s_lidx, s_box);
+        __syncthreads();
+      }
+      const int local = aw - t0;
+      const int base = (local >= 0 && local < nt) ? (local / kChunk) * kChunk : 0;
+      scan(nt, base, c == 0);
+    }
+    update();
+    compact();
+    sort_column(col, cnt);  // the first K keys: the E+1 nearest, in (distance, index) order
+    if (kStats) {
+      const uint32_t cand = __reduce_add_sync(kFull, st_cand);
+      const unsigned vq = __popc(__ballot_sync(kFull, valid));
+      if (lane == 0) {
+        unsigned long long* c = p.stats;
+        atomicAdd(&c[kStatPairsBegun], 32ull * st_begun);
+        atomicAdd(&c[kStatPairsFull], 32ull * st_full);
+        atomicAdd(&c[kStatPairsPruned], 32ull * st_pruned);
+        atomicAdd(&c[kStatCandidates], (unsigned long long)cand);
+        atomicAdd(&c[kStatMergeSlots], 32ull * st_slots);
+        atomicAdd(&c[kStatBruteQueries], (unsigned long long)vq);
+        if (tid == 0) atomicAdd(&c[kStatBruteTiles], 1ull);
+      }
+    }
+
+    // Epilogue: the E+1 nearest (the window kept the query itself out of the
+    // list), simplex weights, prediction, moments.
+    float dd[E + 1];
+    int nb[E + 1];
+#pragma unroll
+    for (int s = 0; s <= E; ++s) {
+      const u64 k = col[s * kThreads];
+      dd[s] = key_dist(k);
+      nb[s] = key_index(k);
+    }
+    finish_tile<E, true>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, s_buf);
+    // the next tile's search starts behind a barrier (this also keeps the
+    // search's registers free of spills)
+    __syncthreads();
   }
-  finish_tile<E, true>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n,
-                       s_buf);
-  // the next tile's search starts behind a barrier (this also keeps the
-  // search's registers free of spills)
-  __syncthreads();
 }
 
 // --------------------------------------------------------------------------
@@ -916,9 +1032,9 @@ __global__ void __launch_bounds__(kThreads, 3) knn_fused_kernel(KnnParams p) {
       continue;
     }
     if (p.variant[E] == 1)
-      process_tile<E, 1, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
+      process_item<E, 1, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
     else
-      process_tile<E, 0, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
+      process_item<E, 0, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
   }
   if (ring_n > 0)
     flush_ring(p, reinterpret_cast<const float*>(smem + kCoordBytes + kBufBytes), s_meta, ring_n);

@@ -86,11 +86,12 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
   UnitDesc* units = reinterpret_cast<UnitDesc*>(scratch + lay.units);
   WorkItem* items = reinterpret_cast<WorkItem*>(scratch + lay.items);
   uint32_t* done = reinterpret_cast<uint32_t*>(scratch + lay.done);
-  const int64_t n_items = (int64_t)c.r * c.n_tiles;
+  const int64_t per_unit = (c.n_tiles + kBruteChunk - 1) / kBruteChunk;  // items per realization
+  const int64_t n_items = (int64_t)c.r * per_unit;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_items;
        w += (int64_t)gridDim.x * blockDim.x) {
-    items[w].unit = (int32_t)(w / c.n_tiles);
-    items[w].tile = (int32_t)(w % c.n_tiles);
+    items[w].unit = (int32_t)(w / per_unit);
+    items[w].tile = (int32_t)((w % per_unit) * kBruteChunk);
   }
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < c.r;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -240,7 +241,7 @@ extern "C" ccm_status ccm_run_noalloc(const float* d_series, int32_t n_series, i
   kp.units = reinterpret_cast<const UnitDesc*>(scratch + lay.units);
   kp.targets = reinterpret_cast<const TargetDesc*>(scratch + lay.target);
   kp.items = reinterpret_cast<const WorkItem*>(scratch + lay.items);
-  kp.n_items = (int64_t)r * n_tiles;
+  kp.n_items = (int64_t)r * ((n_tiles + kBruteChunk - 1) / kBruteChunk);
   kp.lib = reinterpret_cast<const int32_t*>(scratch + lay.lib);
   kp.order = reinterpret_cast<const int32_t*>(scratch + lay.order);
   kp.partials = reinterpret_cast<double*>(scratch + lay.part);

@@ -392,10 +392,15 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
                 ul->item_cost_table.back() += (double)nq * 12.0 * (E + 2) * (double)u.n_m /
                                               (double)L + (double)u.n_targets * nq * 64.0;
               } else {
-                ul->items.push_back(WorkItem{uidx, q});
-                // distance work, staging per library point, per-target epilogue
-                ul->item_cost.push_back((double)L * ((double)nq * (2.0 * E + 1.0) + 64.0 * E) +
-                                        (double)u.n_targets * nq * 64.0);
+                // one item per kBruteChunk tiles: one library staging (when it
+                // fits a shared-memory tile), then per tile the search and the
+                // per-target epilogue
+                if (q % kBruteChunk == 0) {
+                  ul->items.push_back(WorkItem{uidx, q});
+                  ul->item_cost.push_back(64.0 * E * (double)L);
+                }
+                ul->item_cost.back() += (double)L * (double)nq * (2.0 * E + 1.0) +
+                                        (double)u.n_targets * nq * 64.0;
               }
             }
             if (u.table_R == 0) {
@@ -568,6 +573,11 @@ struct ccm_context {
   size_t next_stream = 0, next_fast = 0;
   int max_inflight = 8;
   double batch_pairs = 5.0e10;             // query-library pairs per batch of small jobs
+  // Test hook (CCM_FAULT_INJECT_BATCH, read at creation): the launch of batch
+  // number inject_batch (0-based, in launch order) fails on the host as if a
+  // CUDA call had returned an error; -1: off.  No device work is faulted.
+  int64_t inject_batch = -1;
+  int64_t batches_launched = 0;
   // Pinned staging buffers are pooled: cudaMallocHost/cudaFreeHost may
   // synchronise the device, which would stall polls and new batches behind a
   // running large job.  Size classes are powers of two.
@@ -803,7 +813,7 @@ namespace {
 std::string cache_path() {
   if (const char* p = getenv("CCM_AUTOTUNE_CACHE")) return p;
   const char* home = getenv("HOME");
-  return std::string(home ? home : "/tmp") + "/.cache/ccm_gb300/autotune.tsv";
+  return std::string(home ? home : "/tmp") + "/.cache/ccm_gb300/autotune_v2.tsv";
 }
 
 void load_cache(ccm_context* ctx) {
@@ -878,7 +888,7 @@ ccm_status autotune(ccm_plan_s* pl, cudaStream_t s) {
     float best = 1e30f;
     int best_v = pl->tuning.variant[E], best_ma = pl->tuning.merge_at[E];
     for (int v = 0; v < 2; ++v)
-      for (int ma : {3, 6, 9}) {
+      for (int ma : {2, 4, 8}) {
         Tuning tn = pl->tuning;
         tn.variant[E] = v;
         tn.merge_at[E] = ma;
@@ -951,6 +961,7 @@ ccm_status ccm_context_create(int device, size_t hbm_budget_bytes, ccm_context**
   ctx->device_name = prop.name;
   ctx->sm_count = prop.multiProcessorCount;
   load_cache(ctx.get());
+  if (const char* env = getenv("CCM_FAULT_INJECT_BATCH")) ctx->inject_batch = atoll(env);
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
   *out = ctx.release();
   return CCM_OK;
@@ -1321,7 +1332,9 @@ void CUDART_CB on_batch_done(void* arg) {
 }
 
 // Launch one batch (called by the serving thread without ctx->mu held).
-ccm_status launch_batch(ccm_context* ctx, Batch* b) {
+// `inject`: the fault-injection hook chose this batch; it fails after its
+// arena and series uploads have been enqueued, like a failing CUDA call there.
+ccm_status launch_batch(ccm_context* ctx, Batch* b, bool inject) {
   int64_t series_elems = 0, out = 0;
   for (auto& j : b->jobs) {
     append_units(j->pc, series_elems, out, &b->ul, table_cap(ctx));
@@ -1339,6 +1352,7 @@ ccm_status launch_batch(ccm_context* ctx, Batch* b) {
                              cudaMemcpyHostToDevice, b->stream));
     so += (int64_t)j->pc.V * j->pc.n;
   }
+  if (inject) return fail(CCM_ECUDA, "injected fault (CCM_FAULT_INJECT_BATCH): batch launch failed");
   // Descriptors go through pinned staging: a copy from pageable memory would
   // wait for earlier work on this (reused) stream.
   // (units, work items, order jobs, targets, table jobs, table work items,
@@ -1472,9 +1486,10 @@ void serve(ccm_context* ctx) {
                         ? ctx->fast_streams[ctx->next_fast++ % ctx->fast_streams.size()]
                         : ctx->streams[ctx->next_stream++ % ctx->streams.size()];
         ctx->inflight.push_back(b);
+        const bool inject = ctx->batches_launched++ == ctx->inject_batch;
         lk.unlock();
         b->h_err = static_cast<int32_t*>(pinned_get(ctx, sizeof(int32_t)));
-        ccm_status st = b->h_err ? launch_batch(ctx, b.get())
+        ccm_status st = b->h_err ? launch_batch(ctx, b.get(), inject)
                                  : fail(CCM_ENOMEM, "pinned allocation failed");
         lk.lock();
         if (st != CCM_OK) {

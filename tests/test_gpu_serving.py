@@ -150,3 +150,38 @@ def test_cancel_a_queued_job(ccm):
             wait(ccm, ctx, f, ccm.rho_shape(p))
     finally:
         ccm.ccm_context_destroy(ctx)
+
+
+def test_a_failed_batch_fails_only_its_own_jobs(ccm, monkeypatch):
+    """Host-side fault injection (no device fault): the context's second batch
+    fails its launch as if a CUDA call had returned an error.  Its job reports
+    CCM_ECUDA at ccm_poll; the jobs before and after it, and later batches on
+    the same context, finish with the rho they have when run alone."""
+    jobs = small_jobs(4, seed=13)
+    monkeypatch.setenv("CCM_FAULT_INJECT_BATCH", "1")
+    ctx = ccm.ccm_context_create(0)
+    monkeypatch.delenv("CCM_FAULT_INJECT_BATCH")
+    try:
+        alone = [run_alone(ccm, ctx, j.problem) for j in jobs]
+        results = []
+        for n, (j, ref) in enumerate(zip(jobs, alone)):
+            q = j.problem
+            t = ccm.ccm_submit(ctx, q.series, q.pairs, q.E, q.tau, q.L, q.r, q.seed)
+            wait_times(ccm, ctx, t)               # one job per batch: batch n is job n
+            rho = np.zeros(ccm.rho_shape(q))
+            if n == 1:
+                with pytest.raises(ccm.CCMError) as ei:
+                    ccm.ccm_poll(ctx, t, rho, 0)
+                assert ei.value.status == ccm.CCM_ECUDA
+                assert "injected" in str(ei.value)
+            else:
+                assert ccm.ccm_poll(ctx, t, rho, 0) == ccm.CCM_OK
+                assert np.array_equal(rho, ref), q.name
+                results.append(n)
+        assert results == [0, 2, 3]
+        # the failed batch released its share of the budget: a big job still fits
+        p = I.subproblem(I.sweep_problem(), E=[3], tau=[0], L=[5], r=20)
+        t = ccm.ccm_submit(ctx, p.series, p.pairs, p.E, p.tau, p.L, p.r, p.seed)
+        assert np.array_equal(wait(ccm, ctx, t, ccm.rho_shape(p)), run_alone(ccm, ctx, p))
+    finally:
+        ccm.ccm_context_destroy(ctx)

@@ -49,6 +49,35 @@ def test_noalloc_matches_ccm_run_on_two_calls_in_a_row():
         ccm.ccm_context_destroy(ctx)
 
 
+def test_noalloc_long_manifold_matches_ccm_run():
+    """N = 10^5: a manifold above the one-pass sort size keeps time order here (no
+    scratch for the merge sort) while ccm_run sorts it, and the sampler recomputes
+    its keys per radix pass (more points than fit in shared memory); about 1.3 MB
+    of the fixed scratch.  Two calls in a row, each against ccm_run."""
+    torch = pytest.importorskip("torch")
+    from paper_1905_00565_gb300 import ccm
+    p = I.long_series_problem()
+    j, i, E, tau, L, r = 1, 0, 4, 1, 1000, 4
+    ctx = ccm.ccm_context_create(0)
+    try:
+        plan = ccm.ccm_plan(ctx, p.series.shape, [[j, i]], [E], [tau], [L], r, p.seed)
+        want = np.zeros((1, 1, 1, 1, r))
+        try:
+            ccm.ccm_run(plan, p.series, want)
+        finally:
+            ccm.ccm_plan_destroy(plan)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+    want = want.reshape(-1)
+    s_dev = torch.from_numpy(p.series).cuda()
+    for _ in range(2):
+        rho = torch.full((r,), float("nan"), dtype=torch.float64, device="cuda")
+        ccm.ccm_run_noalloc(s_dev, j, i, E, tau, L, r, p.seed, rho)
+        got = rho.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - want)) <= RHO_TOL
+
+
 def test_noalloc_rejects_a_cell_beyond_its_fixed_scratch():
     torch = pytest.importorskip("torch")
     from paper_1905_00565_gb300 import ccm
