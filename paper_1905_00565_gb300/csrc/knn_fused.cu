@@ -462,9 +462,10 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
 // Stage library points [t0, t0 + nt) of a unit's library (query order) into
 // shared memory: coordinates in packed pairs, indices, and the bounding box
 // of every kChunk consecutive points over the first D coordinates.  The tile
-// is padded to whole chunks with sentinel points (infinite coordinates, index
+// is padded to whole chunks with sentinel points (NaN coordinates, index
 // INT_MAX) that are never selected.  Block-wide; the caller brackets it with
-// barriers.
+// barriers.  Sentinel coordinates are NaN: every distance to a sentinel is
+// NaN, which compares false against any threshold.
 template <int E>
 __device__ __noinline__ void stage_library(const float* sj, const int32_t* lib, int off, int tau,
                                               int t0, int nt, u64* s_coord, int32_t* s_lidx,
@@ -488,18 +489,18 @@ __device__ __noinline__ void stage_library(const float* sj, const int32_t* lib, 
       }
       if (EP > E) cpair[2 * E + half] = 0.f;
     } else {
-      if (a < ntp) {  // sentinel point: infinite distance, never selected
+      if (a < ntp) {  // sentinel point: never selected
         s_lidx[a] = INT_MAX;
         float* cpair = reinterpret_cast<float*>(s_coord + (size_t)pp * EP);
 #pragma unroll
-        for (int e = 0; e < E; ++e) cpair[2 * e + half] = INFINITY;
+        for (int e = 0; e < E; ++e) cpair[2 * e + half] = __int_as_float(0x7fffffff);
         if (EP > E) cpair[2 * E + half] = 0.f;
       }
 #pragma unroll
-      for (int e = 0; e < D; ++e) c0[e] = INFINITY;
+      for (int e = 0; e < D; ++e) c0[e] = __int_as_float(0x7fffffff);
     }
-    // chunk boxes over the first D coordinates: one per half-warp (sentinels
-    // widen only hi)
+    // chunk boxes over the first D coordinates: one per half-warp (fminf and
+    // fmaxf skip the NaN of a sentinel; a chunk always holds a real point)
 #pragma unroll
     for (int e = 0; e < D; ++e) {
       float lo = c0[e], hi = c0[e];
@@ -568,51 +569,74 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
   constexpr int EP = TileShape<E>::EP;
   constexpr int LT = TileShape<E>::LT;
   constexpr int D = TileShape<E>::D;
-  u64* s_coord = reinterpret_cast<u64*>(smem);                                   // [LT/2][EP]
-  int32_t* s_lidx = reinterpret_cast<int32_t*>(smem + (size_t)(LT / 2) * EP * 8);  // [LT]
-  float* s_box = reinterpret_cast<float*>(smem + kCoordBytes - kBoxBytes);       // [LT/kChunk][2D]
-  u64* s_buf = reinterpret_cast<u64*>(smem + kCoordBytes);                      // [kBuf][kThreads]
+  const int n_m = u.n_m, L = u.L, tau = u.tau, W = u.theiler;
+  const bool single = L <= LT;
+  // Shared-memory layout: library indices [LT], chunk boxes [LT/kChunk][2D],
+  // coordinates [LT/2][EP] in the first kCoordBytes, then the candidate
+  // buffer [kBuf][kThreads].  A library that fits one tile takes only the
+  // coordinate rows it needs, and the buffer starts right after them, so its
+  // columns reach up to the prediction ring: wider columns need fewer
+  // compactions.
+  int32_t* s_lidx = reinterpret_cast<int32_t*>(smem);
+  float* s_box = reinterpret_cast<float*>(smem + (size_t)LT * 4);
+  u64* s_coord = reinterpret_cast<u64*>(smem + (size_t)LT * 4 + kBoxBytes);
+  size_t buf_off = kCoordBytes;
+  if (single) {
+    const int ntp = (L + kChunk - 1) / kChunk * kChunk;
+    buf_off = (size_t)LT * 4 + kBoxBytes + (size_t)(ntp / 2) * EP * 8;
+  }
+  u64* s_buf = reinterpret_cast<u64*>(smem + buf_off);
+  const int cap = (int)((kCoordBytes + kBufBytes - buf_off) / (kThreads * 8));  // >= kBuf
   float* s_ring = reinterpret_cast<float*>(smem + kCoordBytes + kBufBytes);      // [kRing][kQT]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n_m = u.n_m, L = u.L, tau = u.tau, W = u.theiler;
   const int off = (E - 1) * tau;
   const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
   const int32_t* lib = p.lib + u.lib_off;
   const int32_t* order = p.order + u.order_off;
   constexpr int kStep = kStepE<E, V>;
   constexpr int kPairs = kStep / 2;
-  constexpr int kRoom = kBuf - kStep;   // a column above this cannot take another step
+  const int room = cap - kStep;   // a column above this cannot take another step
   static_assert(K + kStep <= kBuf, "a cut column must leave room for a step");
-  const int merge_at = max(1, min(p.merge_at[E], kRoom));
+  const int merge_at = max(1, min(p.merge_at[E], room));
   // the first kInit points of a query's scan go straight into its threshold
   constexpr int kInit = (K + kStep - 1) / kStep * kStep;
   static_assert(kInit <= kChunk, "the initial points lie in the first chunk");
   u64* col = s_buf + tid;  // this thread's candidate column
 
-  const bool single = L <= LT;
   const int tile1 = min(u.n_tiles, tile0 + kBruteChunk);
   if (single) {
     __syncthreads();  // the previous item's readers of the tile are done
     stage_library<E>(sj, lib, off, tau, 0, L, s_coord, s_lidx, s_box);
     __syncthreads();
   }
+  // A warp's 32 queries are consecutive positions of the query order.  For
+  // small E (a short search, so the load latency would show) the next tile's
+  // query and coordinates are loaded before this tile's epilogue, so their
+  // latency overlaps it; for larger E the registers are needed elsewhere.
+  constexpr bool kPrefetch = E <= 3;
+  int m_nx;
+  float c_nx[E];
+  auto load_query = [&](int t) {
+    const int ps = t * kQT + tid;
+    m_nx = order[ps < n_m ? ps : n_m - 1];
+#pragma unroll
+    for (int e = 0; e < E; ++e) c_nx[e] = sj[m_nx + off - e * tau];
+  };
+  if (kPrefetch) load_query(tile0);
   for (int tile = tile0; tile < tile1; ++tile) {
-    // A warp's 32 queries are consecutive positions of the query order.
+    if (!kPrefetch) load_query(tile);
     const int pos = tile * kQT + tid;
     const bool valid = pos < n_m;
-    const int m = order[valid ? pos : n_m - 1];
+    const int m = m_nx;
     u64 qc[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const float c = sj[m + off - e * tau];
-      qc[e] = pack2(c, c);
-    }
+    for (int e = 0; e < E; ++e) qc[e] = pack2(c_nx[e], c_nx[e]);
     // Bounding box of the warp's queries over the first D coordinates.
     float qlo[D], qhi[D];
 #pragma unroll
     for (int e = 0; e < D; ++e) {
-      float lo = sj[m + off - e * tau], hi = lo;
+      float lo = c_nx[e], hi = lo;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
@@ -638,8 +662,14 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
         st_cand += (uint32_t)(cnt - done);
         st_slots += (uint32_t)mx;
       }
-      for (int b = 0; b < mx; ++b)
-        if (b < cnt - done) thresh_insert<K>(tl, key_dist(col[(done + b) * kThreads]));
+      for (int b = 0; b < mx; ++b) {
+        // the distance half of the key; a lane with no new key inserts +inf
+        // (a no-op), and a round no lane needs any more is skipped
+        const float x = (b < cnt - done)
+                            ? reinterpret_cast<const float*>(col + (done + b) * kThreads)[1]
+                            : INFINITY;
+        if (__any_sync(kFull, x < tl[K - 1])) thresh_insert<K>(tl, x);
+      }
       done = cnt;
     };
     // keep the keys at or below the threshold (in order)
@@ -657,9 +687,9 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
     };
     auto make_room = [&]() {
       update();
-      if (__any_sync(kFull, cnt > kRoom)) compact();
-      if (__any_sync(kFull, cnt > kRoom)) {  // ties at the threshold: keep the K smallest keys
-        if (cnt > kRoom) {
+      if (__any_sync(kFull, cnt > room)) compact();
+      if (__any_sync(kFull, cnt > room)) {  // ties at the threshold: keep the K smallest keys
+        if (cnt > room) {
           sort_column(col, cnt);
           cnt = done = K;
         }
@@ -668,14 +698,17 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
 
     // Scan the staged points [0, nt) from position `base` (a chunk start),
     // wrapping around; `first`: the scan's first kInit points fill tl.
+    // Scan the staged points [0, nt) chunk by chunk from the chunk at `base`,
+    // wrapping around; `first`: the scan's first kInit points fill tl.
     auto scan = [&](int nt, int base, bool first) {
       const int ntp = (nt + kChunk - 1) / kChunk * kChunk;
-      int i = 0;
+      const int nch = ntp / kChunk;
+      const int c0 = base / kChunk;
+      constexpr int kSteps = kChunk / kStep;  // steps per chunk
       if (first) {
 #pragma unroll
         for (int pp = 0; pp < kInit / 2; ++pp) {
-          int a = base + 2 * pp;
-          a -= (a >= ntp) ? ntp : 0;
+          const int a = base + 2 * pp;
           float d2[2];
           unpack2(sqdist2_range<E, 0, E>(qc, s_coord + (size_t)(a >> 1) * EP, 0ull), d2[0], d2[1]);
 #pragma unroll
@@ -692,21 +725,21 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
           st_begun += kInit;
           st_full += kInit;
         }
-        if (__any_sync(kFull, cnt > kRoom)) make_room();
-        i = kInit;
+        if (__any_sync(kFull, cnt > room)) make_room();
       }
 #pragma unroll 1
-      for (; i < ntp; i += kStep) {
-        int a = base + i;
-        a -= (a >= ntp) ? ntp : 0;
-        if ((a & (kChunk - 1)) == 0) {
+      for (int jc = 0; jc < nch; ++jc) {
+        int c = c0 + jc;
+        c -= (c >= nch) ? nch : 0;
+        const int s0 = (first && jc == 0) ? kInit / kStep : 0;  // steps the fill took
+        if (s0 == 0) {
           // Chunk pruning.  gap_e = max(0, lo_e - qhi_e, qlo_e - hi_e) bounds
           // |q_e - x_e| from below for every query q of the warp and point x of
           // the chunk, in FP32 too (rounding is monotone); summed in the
           // distance's own order over the first D coordinates it bounds every
           // FP32 squared distance between them from below.  A chunk whose bound
           // exceeds every lane's threshold holds no candidate.
-          const float* bx = s_box + (a / kChunk) * 2 * D;
+          const float* bx = s_box + c * 2 * D;
           float lb = 0.f;
 #pragma unroll
           for (int e = 0; e < D; ++e) {
@@ -716,43 +749,61 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
           const float th_max = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(tl[K - 1])));
           if (lb > th_max) {
             if (kStats) st_pruned += kChunk;
-            i += kChunk - kStep;
             continue;
           }
         }
-        if (kStats) st_begun += kStep;
-        const u64* cp = s_coord + (size_t)(a >> 1) * EP;
-        // Partial sums over the first E1 coordinates are lower bounds of the
-        // full FP32 sums (all terms are >= 0 and rounding is monotone), so a
-        // step whose partials are all above every lane's threshold cannot
-        // contribute a candidate and skips the remaining coordinates.
-        u64 r[kPairs];
+        // two steps a chunk (kStep 8) unrolled; four (kStep 4, the larger E)
+        // kept as a loop: unrolled they outgrow the instruction cache
+#pragma unroll(kSteps <= 2 ? kSteps : 1)
+        for (int sp = s0; sp < kSteps; ++sp) {
+          const int a = c * kChunk + sp * kStep;
+          if (kStats) st_begun += kStep;
+          const u64* cp = s_coord + (size_t)(a >> 1) * EP;
+          // Partial sums over the first E1 coordinates are lower bounds of the
+          // full FP32 sums (all terms are >= 0 and rounding is monotone), so a
+          // step whose partials are all above every lane's threshold cannot
+          // contribute a candidate and skips the remaining coordinates.
+          u64 r[kPairs];
 #pragma unroll
-        for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, (kE1<E, V>)>(qc, cp + pp * EP, 0ull);
-        const float th = tl[K - 1];
-        float d[kStep];
+          for (int pp = 0; pp < kPairs; ++pp) r[pp] = sqdist2_range<E, 0, (kE1<E, V>)>(qc, cp + pp * EP, 0ull);
+          const float th = tl[K - 1];
+          float d[kStep];
 #pragma unroll
-        for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
-        if (kStats && (kE1<E, V>) == E) st_full += kStep;
-        if (!__any_sync(kFull, min_all(d) <= th)) continue;
-        if constexpr ((kE1<E, V>) < E) {
-          if (kStats) st_full += kStep;
-#pragma unroll
-          for (int pp = 0; pp < kPairs; ++pp) {
-            r[pp] = sqdist2_range<E, (kE1<E, V>), E>(qc, cp + pp * EP, r[pp]);
-            unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
-          }
+          for (int pp = 0; pp < kPairs; ++pp) unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+          if (kStats && (kE1<E, V>) == E) st_full += kStep;
           if (!__any_sync(kFull, min_all(d) <= th)) continue;
-        }
+          if constexpr ((kE1<E, V>) < E) {
+            if (kStats) st_full += kStep;
 #pragma unroll
-        for (int pt = 0; pt < kStep; ++pt) {
-          if (d[pt] <= th) {
-            const int l = s_lidx[a + pt];
-            // a real point outside the exclusion window (W = 0 drops only m)
-            if (l != INT_MAX && abs(l - m) > W) col[(cnt++) * kThreads] = pack_key(d[pt], l);
+            for (int pp = 0; pp < kPairs; ++pp) {
+              r[pp] = sqdist2_range<E, (kE1<E, V>), E>(qc, cp + pp * EP, r[pp]);
+              unpack2(r[pp], d[2 * pp], d[2 * pp + 1]);
+            }
+            if (!__any_sync(kFull, min_all(d) <= th)) continue;
           }
+          // the step's library indices (one broadcast 16-byte load per four)
+          int li[kStep];
+#pragma unroll
+          for (int q4 = 0; q4 < kStep / 4; ++q4) {
+            const int4 v = *reinterpret_cast<const int4*>(s_lidx + a + 4 * q4);
+            li[4 * q4] = v.x;
+            li[4 * q4 + 1] = v.y;
+            li[4 * q4 + 2] = v.z;
+            li[4 * q4 + 3] = v.w;
+          }
+#pragma unroll
+          for (int pt = 0; pt < kStep; ++pt) {
+            // at or below the threshold (never a sentinel: NaN), outside the
+            // exclusion window |l - m| <= W (W = 0 drops only m itself, and
+            // the unsigned form tests both sides at once); appended without a
+            // branch
+            const bool take = (d[pt] <= th) &
+                              ((unsigned)li[pt] - (unsigned)m + (unsigned)W > 2u * (unsigned)W);
+            if (take) col[cnt * kThreads] = pack_key(d[pt], li[pt]);
+            cnt += take ? 1 : 0;
+          }
+          if (__any_sync(kFull, cnt - done >= merge_at || cnt > room)) make_room();
         }
-        if (__any_sync(kFull, cnt - done >= merge_at || cnt > kRoom)) make_room();
       }
     };
 
@@ -803,6 +854,7 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
       dd[s] = key_dist(k);
       nb[s] = key_index(k);
     }
+    if (kPrefetch && tile + 1 < tile1) load_query(tile + 1);
     finish_tile<E, true>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, s_buf);
     // the next tile's search starts behind a barrier (this also keeps the
     // search's registers free of spills)

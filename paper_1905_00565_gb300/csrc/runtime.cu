@@ -888,7 +888,7 @@ ccm_status autotune(ccm_plan_s* pl, cudaStream_t s) {
     float best = 1e30f;
     int best_v = pl->tuning.variant[E], best_ma = pl->tuning.merge_at[E];
     for (int v = 0; v < 2; ++v)
-      for (int ma : {2, 4, 8}) {
+      for (int ma : {1, 2, 4, 8}) {
         Tuning tn = pl->tuning;
         tn.variant[E] = v;
         tn.merge_at[E] = ma;
