@@ -170,7 +170,8 @@ cudaError_t launch_order(const float* series, const OrderJob* jobs, int64_t n_jo
 
 // Distance indexing table (table.cu).
 cudaError_t table_prepare();
-cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs,
+// One launch builds the tables of jobs[0..n_jobs), all of embedding dimension E.
+cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs, int E,
                                int max_nm, int max_R, const int32_t* order, void* table,
                                float* table_d2, int table_u16, cudaStream_t s);
 

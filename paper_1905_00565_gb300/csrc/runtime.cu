@@ -159,9 +159,10 @@ struct UnitList {
   std::vector<double> item_cost_table;
   int64_t lib_total = 0, part_total = 0, order_total = 0, table_total = 0;
   int64_t order_scratch_total = 0;    // 64-bit keys for sorting manifolds above kOrderMaxSort
-  // Table jobs are sorted by R (sort_items) and built one launch per sort
-  // size (the power of two at or above R): a launch's shared memory per warp
-  // follows its own largest row, so short rows run more warps per SM.
+  // Table jobs are sorted by (sort size, E) (sort_items) and built one launch
+  // per sort size (the power of two at or above R) and E: a launch's shared
+  // memory per warp follows its own largest row, so short rows run more warps
+  // per SM, and its registers follow its E.
   static int table_rcap(int R) {
     int rc = 32;
     while (rc < R) rc <<= 1;
@@ -170,7 +171,9 @@ struct UnitList {
   int table_groups() const {
     int g = 0;
     for (size_t q = 0; q < tables.size(); ++q)
-      if (q == 0 || table_rcap(tables[q].R) != table_rcap(tables[q - 1].R)) ++g;
+      if (q == 0 || table_rcap(tables[q].R) != table_rcap(tables[q - 1].R) ||
+          tables[q].E != tables[q - 1].E)
+        ++g;
     return g;
   }
   double brute_flops = 0.0;           // 3E per pair of the units searched by brute force
@@ -431,8 +434,12 @@ void sort_by_cost(std::vector<WorkItem>* items, const std::vector<double>& cost)
 }
 
 void sort_items(UnitList* ul) {
-  std::stable_sort(ul->tables.begin(), ul->tables.end(),
-                   [](const TableJob& a, const TableJob& b) { return a.R < b.R; });
+  std::stable_sort(ul->tables.begin(), ul->tables.end(), [](const TableJob& a, const TableJob& b) {
+    const int ra = UnitList::table_rcap(a.R), rb = UnitList::table_rcap(b.R);
+    if (ra != rb) return ra < rb;
+    if (a.E != b.E) return a.E < b.E;
+    return a.R < b.R;
+  });
   // Brute-force items: grouped by E (one single-E kernel launch per group,
   // in the stream's order), larger items first within a group.
   {
@@ -730,17 +737,19 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                         reinterpret_cast<int32_t*>(base + ar.order),
                         reinterpret_cast<unsigned long long*>(base + ar.order_scratch), s));
   CCM_CUDA(enqueue_obs(base, ar, ul, s));
-  for (size_t g0 = 0; g0 < ul.tables.size();) {  // one launch per sort size
-    const int rc = UnitList::table_rcap(ul.tables[g0].R);
+  for (size_t g0 = 0; g0 < ul.tables.size();) {  // one launch per (sort size, E)
+    const int rc = UnitList::table_rcap(ul.tables[g0].R), te = ul.tables[g0].E;
     size_t g1 = g0;
     int nm = 0, rmax = 0;
-    for (; g1 < ul.tables.size() && UnitList::table_rcap(ul.tables[g1].R) == rc; ++g1) {
+    for (; g1 < ul.tables.size() && UnitList::table_rcap(ul.tables[g1].R) == rc &&
+           ul.tables[g1].E == te;
+         ++g1) {
       nm = std::max(nm, ul.tables[g1].n_m);
       rmax = std::max(rmax, ul.tables[g1].R);
     }
     CCM_CUDA(launch_table_build(reinterpret_cast<const float*>(base + ar.series),
                                 reinterpret_cast<const TableJob*>(base + ar.tables) + g0,
-                                (int64_t)(g1 - g0), nm, rmax,
+                                (int64_t)(g1 - g0), te, nm, rmax,
                                 reinterpret_cast<const int32_t*>(base + ar.order),
                                 base + ar.table, reinterpret_cast<float*>(base + ar.table_d2),
                                 ul.table_u16(), s));

@@ -21,7 +21,10 @@
 // scan reads the E+1 distances it needs instead of recomputing them from E
 // scattered coordinates each.
 //
-// Build: one warp per query position.  A histogram of the top 11 bits of the
+// Build: one warp per query position, one kernel per E (its registers follow
+// that E), the distance loops unrolled four ways so that a lane has four
+// independent points' loads in flight (the series is read from L1: the build
+// is bound by load latency, not bandwidth).  A histogram of the top 11 bits of the
 // FP32 bit patterns of all N_m squared distances finds the bin b1 holding rank
 // R; a second pass collects every entry below b1 (all of them belong to the
 // row) and the entries of b1; both are sorted by (bits, index) (bitonic sorts
@@ -38,6 +41,11 @@ namespace ccm {
 namespace {
 
 constexpr int kTableWarps = 8;  // query positions per CTA
+constexpr int kUnroll = 4;      // points per lane per distance-loop iteration
+constexpr int kSampleMinNm = 32768;  // manifolds from this size build rows from a sample threshold
+constexpr int kSampleStride = 8;     // the sample: every 8th manifold point
+constexpr int kStageChunk = 2048;    // manifold points per staged series chunk
+constexpr int kStageHalo = 1024;     // lag span (E-1)tau up to which the series is staged
 constexpr int kTableBoundary = 512;  // boundary-bin entries sorted directly (else refined)
 
 __host__ __device__ constexpr size_t table_warp_bytes(int rcap) {
@@ -117,25 +125,171 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long* keys, int n) {
   }
 }
 
+// The same distance with the coordinates read from a staged chunk of the
+// series: stage[j] = s[base + j], xl = x - base.
 template <int E>
-__device__ void build_row(const float* s, const TableJob& jb, int pos, const int32_t* order,
-                          void* table, float* table_d2, int u16, uint32_t* hist,
-                          unsigned long long* keys,
-                          unsigned long long* bnd, uint32_t* cnt) {
+__device__ __forceinline__ uint32_t d2_bits_staged(const float* stage, int off, int tau,
+                                                   const float (&q)[E], int xl) {
+  float diff = __fsub_rn(q[0], stage[xl + off]);
+  float acc = __fmul_rn(diff, diff);
+#pragma unroll
+  for (int e = 1; e < E; ++e) {
+    diff = __fsub_rn(q[e], stage[xl + off - e * tau]);
+    acc = __fmaf_rn(diff, diff, acc);
+  }
+  return __float_as_uint(acc);
+}
+
+// One row (query position pos) of a table, by one warp.  `row`: pos is a
+// query of the job (a warp without one takes part in the block-wide staging
+// of the sampled path only); `stage`: shared memory for kStageChunk + kStageHalo
+// series values, or null.
+template <int E>
+__device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
+                          const int32_t* order, void* table, float* table_d2, int u16,
+                          uint32_t* hist, unsigned long long* keys, unsigned long long* bnd,
+                          uint32_t* cnt, int region_keys, float* stage) {
   const int lane = threadIdx.x & 31;
   const unsigned below_lane = (1u << lane) - 1u;
   const int n_m = jb.n_m, tau = jb.tau, off = (E - 1) * tau, R = jb.R;
-  const int m = order[jb.order_off + pos];
+  const int m = order[jb.order_off + (row ? pos : 0)];
   float q[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) q[e] = s[m + off - e * tau];
   auto key_of = [](uint32_t bits, int x) { return ((unsigned long long)bits << 32) | (unsigned)x; };
 
+  // Long manifolds: one collecting pass below a threshold estimated from a
+  // sample of one point in kSampleStride, taken as runs of 32 consecutive
+  // points spread over the manifold (coalesced loads; two histogram levels give
+  // the sample's k-th smallest distance to 21 bits; k is chosen so that about
+  // (R + C)/2 of all points fall below it, C the largest power of two the
+  // warp's key region holds), then one sort of the collected keys.  If the
+  // count misses [R, C] the exact passes below run instead.  The collecting
+  // pass reads the series through shared memory, chunk by chunk, staged once
+  // for the CTA's eight rows (the decision is the same for the whole CTA).
+  bool sampled = false;
+  int C = 1;
+  while (2 * C <= region_keys) C <<= 1;
+  if (n_m >= kSampleMinNm && R < C) {
+   uint32_t T = 0u;
+   if (row) {
+    const int runs = n_m / (32 * kSampleStride);           // whole runs inside the manifold
+    const int S = runs * 32;
+    const int k = (int)(((int64_t)(R + C) / 2 * S + n_m - 1) / n_m);  // >= 1, < S
+    for (int b = lane; b < 2048; b += 32) hist[b] = 0u;
+    __syncwarp();
+    // sample point i: run i/32 (runs kSampleStride*32 points apart), offset i%32
+    auto sample_x = [](int i) { return (i >> 5) * (32 * kSampleStride) + (i & 31); };
+    // runs are far apart (L2 latency): four runs' loads in flight per lane
+    for (int i0 = 0; i0 < S; i0 += 32 * kUnroll) {  // S is a multiple of 32: whole warps
+      uint32_t b[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + 32 * u + lane;
+        b[u] = (i < S) ? d2_bits<E>(s, off, tau, q, sample_x(i)) >> 21 : 0xffffffffu;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        // lanes that share a bin add once (the coarse bins are crowded)
+        const unsigned same = __match_any_sync(kFullMask, b[u]);
+        if (b[u] != 0xffffffffu && lane == __ffs(same) - 1)
+          atomicAdd(&hist[b[u]], (uint32_t)__popc(same));
+      }
+    }
+    __syncwarp();
+    int bs1, bs2;
+    uint32_t bef1, c1, bef2, c2;
+    select_bin(hist, 2048, k, &bs1, &bef1, &c1);
+    __syncwarp();
+    for (int b = lane; b < 1024; b += 32) hist[b] = 0u;
+    __syncwarp();
+    for (int i0 = lane; i0 < S; i0 += 32 * kUnroll) {
+      uint32_t bits[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + 32 * u;
+        bits[u] = (i < S) ? d2_bits<E>(s, off, tau, q, sample_x(i)) : 0xffffffffu;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if ((bits[u] >> 21) == (uint32_t)bs1) atomicAdd(&hist[(bits[u] >> 11) & 1023u], 1u);
+    }
+    __syncwarp();
+    select_bin(hist, 1024, k - (int)bef1, &bs2, &bef2, &c2);
+    T = ((uint32_t)bs1 << 21) | ((uint32_t)bs2 << 11) | 0x7ffu;
+   }
+    if (lane == 0) cnt[0] = 0u;
+    __syncwarp();
+    if (stage) {
+      for (int base = 0; base < n_m; base += kStageChunk) {
+        const int len = min(kStageChunk, n_m - base);
+        __syncthreads();  // the previous chunk has been read
+        for (int i = threadIdx.x; i < len + off; i += blockDim.x) stage[i] = s[base + i];
+        __syncthreads();
+        if (row) {
+          for (int x0 = lane; x0 < len; x0 += 32 * kUnroll) {
+            uint32_t bits[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+              const int xl = x0 + 32 * u;
+              bits[u] = (xl < len) ? d2_bits_staged<E>(stage, off, tau, q, xl) : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+              if (bits[u] <= T && x0 + 32 * u < len) {
+                const uint32_t at = atomicAdd(&cnt[0], 1u);
+                if (at < (uint32_t)C) keys[at] = key_of(bits[u], base + x0 + 32 * u);
+              }
+            }
+          }
+        }
+      }
+    } else if (row) {
+    for (int x0 = lane; x0 < n_m; x0 += 32 * kUnroll) {
+      uint32_t bits[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int x = x0 + 32 * u;
+        bits[u] = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (bits[u] <= T && x0 + 32 * u < n_m) {
+          const uint32_t at = atomicAdd(&cnt[0], 1u);
+          if (at < (uint32_t)C) keys[at] = key_of(bits[u], x0 + 32 * u);
+        }
+      }
+    }
+    }
+    __syncwarp();
+    const int c = (int)cnt[0];
+    if (row && c >= R && c <= C) {
+      int p2 = 32;
+      while (p2 < c) p2 <<= 1;
+      for (int i = c + lane; i < p2; i += 32) keys[i] = ~0ull;
+      __syncwarp();
+      warp_bitonic(keys, p2);
+      sampled = true;
+    }
+    __syncwarp();
+  }
+  if (!row) return;
+  if (!sampled) {
   // Pass 1: histogram of the top 11 bits (non-negative floats order like
   // their bit patterns); the bin b1 holding rank R.
   for (int b = lane; b < 2048; b += 32) hist[b] = 0u;
   __syncwarp();
-  for (int x = lane; x < n_m; x += 32) atomicAdd(&hist[d2_bits<E>(s, off, tau, q, x) >> 21], 1u);
+  for (int x0 = lane; x0 < n_m; x0 += 32 * kUnroll) {
+    uint32_t bits[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int x = x0 + 32 * u;
+      bits[u] = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (x0 + 32 * u < n_m) atomicAdd(&hist[bits[u] >> 21], 1u);
+  }
   __syncwarp();
   int b1;
   uint32_t below1, in_b1;
@@ -150,11 +304,20 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
     // sorted by their full keys below, so the arrival order does not matter
     if (lane == 0) cnt[0] = cnt[1] = 0u;
     __syncwarp();
-    for (int x = lane; x < n_m; x += 32) {
-      const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
-      const uint32_t bin = bits >> 21;
-      if (bin < (uint32_t)b1) keys[atomicAdd(&cnt[0], 1u)] = key_of(bits, x);
-      else if (bin == (uint32_t)b1) bnd[atomicAdd(&cnt[1], 1u)] = key_of(bits, x);
+    for (int x0 = lane; x0 < n_m; x0 += 32 * kUnroll) {
+      uint32_t bits[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int x = x0 + 32 * u;
+        bits[u] = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int x = x0 + 32 * u;
+        const uint32_t bin = bits[u] >> 21;
+        if (bin < (uint32_t)b1) keys[atomicAdd(&cnt[0], 1u)] = key_of(bits[u], x);
+        else if (bin == (uint32_t)b1 && x < n_m) bnd[atomicAdd(&cnt[1], 1u)] = key_of(bits[u], x);
+      }
     }
     __syncwarp();
     const uint32_t nb = cnt[1];
@@ -183,9 +346,17 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
       const uint32_t dm = (uint32_t)nbins - 1u;
       for (int b = lane; b < nbins; b += 32) hist[b] = 0u;
       __syncwarp();
-      for (int x = lane; x < n_m; x += 32) {
-        const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
-        if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> sh) & dm], 1u);
+      for (int x0 = lane; x0 < n_m; x0 += 32 * kUnroll) {
+        uint32_t bits[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int x = x0 + 32 * u;
+          bits[u] = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+          if (x0 + 32 * u < n_m && (bits[u] & mask) == prefix)
+            atomicAdd(&hist[(bits[u] >> sh) & dm], 1u);
       }
       __syncwarp();
       int bin;
@@ -219,6 +390,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
     __syncwarp();
     warp_bitonic(keys, rcap);
   }
+  }
   __syncwarp();
   const int64_t base = jb.table_off + (int64_t)pos * 4;
   for (int r = lane; r < R; r += 32)  // each entry's squared distance, beside it
@@ -235,15 +407,17 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, const int
   __syncwarp();
 }
 
+template <int E>
 __global__ void __launch_bounds__(kTableWarps * 32, 2)
 table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
                    float* table_d2, int u16, int rcap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_cnt[kTableWarps][2];  // per warp: entries below b1, entries of b1
   const TableJob jb = jobs[blockIdx.y];
+  if (jb.E != E) return;  // the same job for the whole CTA
   const int warp = threadIdx.x >> 5;
   const int pos = blockIdx.x * kTableWarps + warp;
-  if (pos >= jb.n_m) return;  // whole warp leaves; no block-wide barrier follows
+  if (blockIdx.x * kTableWarps >= jb.n_m) return;  // the whole CTA past this job's rows
   // per warp: the 2048 histogram bins, overlapping the rcap row keys and the
   // kTableBoundary keys of the boundary bin
   unsigned char* mine = smem + warp * table_warp_bytes(rcap);
@@ -251,26 +425,37 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(mine);
   unsigned long long* bnd = keys + rcap;
   const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
-  switch (jb.E) {
-#define CCM_TB(EV) \
-  case EV: build_row<EV>(s, jb, pos, order, table, table_d2, u16, hist, keys, bnd, s_cnt[warp]); break;
-    CCM_TB(1) CCM_TB(2) CCM_TB(3) CCM_TB(4) CCM_TB(5)
-    CCM_TB(6) CCM_TB(7) CCM_TB(8) CCM_TB(9) CCM_TB(10)
-#undef CCM_TB
-    default: break;
-  }
+  // staged collecting pass from E = 5 (below that the chunk barriers cost
+  // more than the loads they save)
+  float* stage = (E >= 5 && (E - 1) * jb.tau <= kStageHalo)
+                     ? reinterpret_cast<float*>(smem + kTableWarps * table_warp_bytes(rcap))
+                     : nullptr;
+  build_row<E>(s, jb, pos, pos < jb.n_m, order, table, table_d2, u16, hist, keys, bnd,
+               s_cnt[warp], (int)(table_warp_bytes(rcap) / 8), stage);
 }
 
-size_t table_smem(int rcap) { return (size_t)kTableWarps * table_warp_bytes(rcap); }
+size_t table_smem(int rcap) {
+  return (size_t)kTableWarps * table_warp_bytes(rcap) + (kStageChunk + kStageHalo) * sizeof(float);
+}
 
 }  // namespace
 
+#define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+
 cudaError_t table_prepare() {
-  return cudaFuncSetAttribute(table_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)table_smem(kTableMaxR));
+#define CCM_TBPREP(EV)                                                                   \
+  {                                                                                      \
+    const cudaError_t e = cudaFuncSetAttribute(                                          \
+        table_build_kernel<EV>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+        (int)table_smem(kTableMaxR));                                                    \
+    if (e != cudaSuccess) return e;                                                      \
+  }
+  CCM_FOR_E(CCM_TBPREP)
+#undef CCM_TBPREP
+  return cudaSuccess;
 }
 
-cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs,
+cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs, int E,
                                int max_nm, int max_R, const int32_t* order, void* table,
                                float* table_d2, int table_u16, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
@@ -278,9 +463,15 @@ cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_
   while (rcap < max_R) rcap <<= 1;
   if (rcap > kTableMaxR) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((max_nm + kTableWarps - 1) / kTableWarps), (unsigned)n_jobs);
-  table_build_kernel<<<grid, kTableWarps * 32, table_smem(rcap), s>>>(
-      series, jobs, order, table, table_d2, table_u16, rcap);
-  return cudaGetLastError();
+#define CCM_TBLAUNCH(EV)                                                                 \
+  if (E == EV) {                                                                         \
+    table_build_kernel<EV><<<grid, kTableWarps * 32, table_smem(rcap), s>>>(             \
+        series, jobs, order, table, table_d2, table_u16, rcap);                          \
+    return cudaGetLastError();                                                           \
+  }
+  CCM_FOR_E(CCM_TBLAUNCH)
+#undef CCM_TBLAUNCH
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace ccm
