@@ -22,9 +22,7 @@
 // scattered coordinates each.
 //
 // Build: one warp per query position, one kernel per E (its registers follow
-// that E), the distance loops unrolled four ways so that a lane has four
-// independent points' loads in flight (the series is read from L1: the build
-// is bound by load latency, not bandwidth).  A histogram of the top 11 bits of the
+// that E).  A histogram of the top 11 bits of the
 // FP32 bit patterns of all N_m squared distances finds the bin b1 holding rank
 // R; a second pass collects every entry below b1 (all of them belong to the
 // row) and the entries of b1; both are sorted by (bits, index) (bitonic sorts
@@ -279,17 +277,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
   // their bit patterns); the bin b1 holding rank R.
   for (int b = lane; b < 2048; b += 32) hist[b] = 0u;
   __syncwarp();
-  for (int x0 = lane; x0 < n_m; x0 += 32 * kUnroll) {
-    uint32_t bits[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int x = x0 + 32 * u;
-      bits[u] = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (x0 + 32 * u < n_m) atomicAdd(&hist[bits[u] >> 21], 1u);
-  }
+  for (int x = lane; x < n_m; x += 32) atomicAdd(&hist[d2_bits<E>(s, off, tau, q, x) >> 21], 1u);
   __syncwarp();
   int b1;
   uint32_t below1, in_b1;
@@ -304,20 +292,11 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
     // sorted by their full keys below, so the arrival order does not matter
     if (lane == 0) cnt[0] = cnt[1] = 0u;
     __syncwarp();
-    for (int x0 = lane; x0 < n_m; x0 += 32 * kUnroll) {
-      uint32_t bits[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int x = x0 + 32 * u;
-        bits[u] = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int x = x0 + 32 * u;
-        const uint32_t bin = bits[u] >> 21;
-        if (bin < (uint32_t)b1) keys[atomicAdd(&cnt[0], 1u)] = key_of(bits[u], x);
-        else if (bin == (uint32_t)b1 && x < n_m) bnd[atomicAdd(&cnt[1], 1u)] = key_of(bits[u], x);
-      }
+    for (int x = lane; x < n_m; x += 32) {
+      const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
+      const uint32_t bin = bits >> 21;
+      if (bin < (uint32_t)b1) keys[atomicAdd(&cnt[0], 1u)] = key_of(bits, x);
+      else if (bin == (uint32_t)b1) bnd[atomicAdd(&cnt[1], 1u)] = key_of(bits, x);
     }
     __syncwarp();
     const uint32_t nb = cnt[1];
@@ -346,17 +325,9 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
       const uint32_t dm = (uint32_t)nbins - 1u;
       for (int b = lane; b < nbins; b += 32) hist[b] = 0u;
       __syncwarp();
-      for (int x0 = lane; x0 < n_m; x0 += 32 * kUnroll) {
-        uint32_t bits[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int x = x0 + 32 * u;
-          bits[u] = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-          if (x0 + 32 * u < n_m && (bits[u] & mask) == prefix)
-            atomicAdd(&hist[(bits[u] >> sh) & dm], 1u);
+      for (int x = lane; x < n_m; x += 32) {
+        const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
+        if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> sh) & dm], 1u);
       }
       __syncwarp();
       int bin;
@@ -410,7 +381,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
 template <int E>
 __global__ void __launch_bounds__(kTableWarps * 32, 2)
 table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
-                   float* table_d2, int u16, int rcap) {
+                   float* table_d2, int u16, int rcap, int staged) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_cnt[kTableWarps][2];  // per warp: entries below b1, entries of b1
   const TableJob jb = jobs[blockIdx.y];
@@ -426,16 +397,17 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
   unsigned long long* bnd = keys + rcap;
   const float* s = series + jb.series_off + (int64_t)jb.j * jb.n;
   // staged collecting pass from E = 5 (below that the chunk barriers cost
-  // more than the loads they save)
-  float* stage = (E >= 5 && (E - 1) * jb.tau <= kStageHalo)
+  // more than the loads they save); the launch reserved the space
+  float* stage = (staged && (E - 1) * jb.tau <= kStageHalo)
                      ? reinterpret_cast<float*>(smem + kTableWarps * table_warp_bytes(rcap))
                      : nullptr;
   build_row<E>(s, jb, pos, pos < jb.n_m, order, table, table_d2, u16, hist, keys, bnd,
                s_cnt[warp], (int)(table_warp_bytes(rcap) / 8), stage);
 }
 
-size_t table_smem(int rcap) {
-  return (size_t)kTableWarps * table_warp_bytes(rcap) + (kStageChunk + kStageHalo) * sizeof(float);
+size_t table_smem(int rcap, bool staged) {
+  return (size_t)kTableWarps * table_warp_bytes(rcap) +
+         (staged ? (kStageChunk + kStageHalo) * sizeof(float) : 0);
 }
 
 }  // namespace
@@ -447,7 +419,7 @@ cudaError_t table_prepare() {
   {                                                                                      \
     const cudaError_t e = cudaFuncSetAttribute(                                          \
         table_build_kernel<EV>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
-        (int)table_smem(kTableMaxR));                                                    \
+        (int)table_smem(kTableMaxR, true));                                              \
     if (e != cudaSuccess) return e;                                                      \
   }
   CCM_FOR_E(CCM_TBPREP)
@@ -463,10 +435,11 @@ cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_
   while (rcap < max_R) rcap <<= 1;
   if (rcap > kTableMaxR) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((max_nm + kTableWarps - 1) / kTableWarps), (unsigned)n_jobs);
+  const int staged = (E >= 5 && max_nm >= kSampleMinNm) ? 1 : 0;
 #define CCM_TBLAUNCH(EV)                                                                 \
   if (E == EV) {                                                                         \
-    table_build_kernel<EV><<<grid, kTableWarps * 32, table_smem(rcap), s>>>(             \
-        series, jobs, order, table, table_d2, table_u16, rcap);                          \
+    table_build_kernel<EV><<<grid, kTableWarps * 32, table_smem(rcap, staged), s>>>(     \
+        series, jobs, order, table, table_d2, table_u16, rcap, staged);                  \
     return cudaGetLastError();                                                           \
   }
   CCM_FOR_E(CCM_TBLAUNCH)
