@@ -152,6 +152,23 @@ enum : int {
 constexpr int kDefaultMergeAt = 4;
 constexpr int kDefaultVariant = 1;
 
+// Simplex weight (paper Sect. 2.1) of a neighbour at squared distance d2 when
+// the nearest is at distance d1 (> 0; inv_d1 = 1/d1): u = exp(-d/d1), raised
+// to the floor f.  d1 = 0 takes the limit: 1 for d = 0, else 0.  Shared by the
+// fused kernels and the plain comparator so that all compute the same bits;
+// FP32 with the hardware square root and exponential (relative error near
+// 1e-7, far inside the 1e-5 the predictions are checked to).
+__device__ __forceinline__ float sqrt_hw(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float simplex_u(float d2, float d1, float inv_d1, float wfloor) {
+  const float d = sqrt_hw(d2);
+  const float u = (d1 > 0.f) ? __expf(-__fmul_rn(d, inv_d1)) : ((d == 0.f) ? 1.f : 0.f);
+  return fmaxf(u, wfloor);
+}
+
 // Error flag values written by kernels.
 constexpr int32_t kErrBadUnit = 1;
 constexpr int32_t kErrSampler = 2;

@@ -408,16 +408,18 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   const int off = (E - 1) * u.tau;
   const int nq = min(kQT, n_m - tile * kQT);  // valid queries of this tile (>= 1)
   // Simplex weights (Sect. 2.1), once per query for every target.  Every
-  // floating-point step below is an explicit round-to-nearest operation, so
-  // the brute-force and table kernels (and every batch) produce the same bits.
-  const float d1 = __fsqrt_rn(dd[0]);
+  // floating-point step below is a fixed operation (explicit rounding or a
+  // hardware approximation that is the same everywhere), so the brute-force
+  // and table kernels, the plain comparator and every batch produce the same
+  // bits.
+  const float d1 = sqrt_hw(dd[0]);
+  const float inv_d1 = (d1 > 0.f) ? __frcp_rn(d1) : 0.f;
   float w[E + 1];
   int nbc[E + 1];
   float usum = 0.f;
 #pragma unroll
   for (int s = 0; s <= E; ++s) {
-    const float di = __fsqrt_rn(dd[s]);
-    w[s] = fmaxf((d1 > 0.f) ? expf(-__fdiv_rn(di, d1)) : ((di == 0.f) ? 1.f : 0.f), u.wfloor);
+    w[s] = simplex_u(dd[s], d1, inv_d1, u.wfloor);
     usum = __fadd_rn(usum, w[s]);
     // an unfilled slot (only possible with non-finite device input) reads, and
     // is reported, in bounds
