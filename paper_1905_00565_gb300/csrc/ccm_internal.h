@@ -65,11 +65,17 @@ constexpr int kObsStride = 264;        // doubles per record (64-byte multiple)
 // One work item of the fused kernels: query tiles [tile, tile + chunk) of a
 // unit (chunk = kBruteChunk for the brute-force kernel, kTableChunk for the
 // table kernel; the last item of a unit may hold fewer tiles).
+// A table item may cover `count` consecutive realizations of one cell (units
+// unit .. unit + count - 1): one walk of each query's table row serves all of
+// them.  Brute-force items have count 1.
 struct WorkItem {
   int32_t unit;
   int32_t tile;
+  int32_t count;
 };
 constexpr int kBruteChunk = 8;         // query tiles per brute-force work item (one staging)
+constexpr int kTableGroup = 3;         // realizations per grouped table item, at most
+constexpr int kTableGroupMaxNm = 32768;  // grouping needs a byte membership map (bit b: realization b)
 
 // Query order job: one per (job, library variable, E, tau).
 struct OrderJob {

@@ -885,66 +885,80 @@ __device__ __forceinline__ float d2_point(const float* sj, int off, int tau, con
 }
 
 // Shared memory of the table kernel: the epilogue's ring of predictions, the hits
-// of every query (slot-major, one column per thread), then the library
+// of every query for up to kTableGroup realizations (realization-major, then
+// slot-major, one column per thread), then the library
 // membership map: one byte per manifold point when the manifold has at most
-// kByteMapMax points (a load and a compare per table entry), else one bit.
+// kByteMapMax points (bit b: the point is in realization b's library; one load
+// per table entry), else one bit (one realization).
 constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
 constexpr int kByteMapMax = 32768;
 // A hit is stored as (rank << kHitRankShift) | manifold index.
 constexpr int kHitRankShift = 20;
 static_assert(kTableMaxNm <= (1 << kHitRankShift), "manifold index must fit below the rank");
 static_assert(kTableMaxR <= (1 << (31 - kHitRankShift)), "rank must fit in the hit word");
+static_assert(kTableGroupMaxNm <= kByteMapMax, "grouped table items need the byte map");
+static_assert(kTableGroup <= 4, "four bits per rank in the walk's member mask");
 
 template <int E, bool kStats>
-__device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int unit, int tile0,
+__device__ void process_table_item(const KnnParams& p, int unit0, int count, int tile0,
                                    unsigned char* smem, RingMeta* meta, int& ring_n) {
+  // `count` consecutive realizations of one cell (the same manifold, table, L
+  // and target; count > 1 only with a byte map): one walk of each query's row
+  // finds the E+1 nearest members of every one of them.
+  constexpr int K = E + 1;
   const int tid = threadIdx.x;
-  const int n_m = u.n_m, L = u.L, tau = u.tau, R = u.table_R, W = u.theiler;
+  const UnitDesc u0 = p.units[unit0];
+  const int n_m = u0.n_m, L = u0.L, tau = u0.tau, R = u0.table_R, W = u0.theiler;
   const int off = (E - 1) * tau;
-  const float* sj = p.series + u.series_off + (int64_t)u.j * u.n;
-  const int32_t* lib = p.lib + u.lib_off;
+  const float* sj = p.series + u0.series_off + (int64_t)u0.j * u0.n;
   float* s_ring = reinterpret_cast<float*>(smem);
-  int32_t* s_hit = reinterpret_cast<int32_t*>(smem + kRingBytes);
-  unsigned char* map = smem + kRingBytes + kHitBytes;
+  int32_t* s_hit = reinterpret_cast<int32_t*>(smem + kRingBytes);  // [count][K][kThreads]
+  unsigned char* map = smem + kRingBytes + kTableGroup * kHitBytes;
   const bool bytes = n_m <= kByteMapMax;
   const int words = bytes ? (n_m + 3) >> 2 : (n_m + 31) >> 5;  // 32-bit words of the map
   uint32_t* mw = reinterpret_cast<uint32_t*>(map);
-  // Library membership, once for the item's tiles.
+  // Library membership, once for the item's tiles: byte x holds bit b when
+  // point x is in realization b's library (a bitmap of one realization for
+  // manifolds above kByteMapMax points).
   __syncthreads();  // the previous item's readers of the map are done
   for (int w = tid; w < words; w += kThreads) mw[w] = 0u;
   __syncthreads();
-  for (int a = tid; a < L; a += kThreads) {
-    const int l = lib[a];
-    if (bytes) map[l] = 1;
-    else atomicOr(&mw[l >> 5], 1u << (l & 31));
+  for (int b = 0; b < count; ++b) {
+    const int32_t* lib = p.lib + p.units[unit0 + b].lib_off;
+    for (int a = tid; a < L; a += kThreads) {
+      const int l = lib[a];
+      if (!bytes) atomicOr(&mw[l >> 5], 1u << (l & 31));
+      else if (count == 1) map[l] = 1;
+      else atomicOr(&mw[l >> 2], (1u << b) << (8 * (l & 3)));
+    }
   }
   __syncthreads();
 
-  const int tile1 = min(u.n_tiles, tile0 + kTableChunk);
+  const int tile1 = min(u0.n_tiles, tile0 + kTableChunk);
   const int groups = R >> 2;  // groups of four ranks
+  const uint32_t all = (1u << count) - 1u;
   for (int tile = tile0; tile < tile1; ++tile) {
     const int pos = tile * kQT + tid;
     const bool valid = pos < n_m;
-    const int m = p.order[u.order_off + (valid ? pos : n_m - 1)];
-    float q[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
+    const int m = p.order[u0.order_off + (valid ? pos : n_m - 1)];
 
-    // Walk the row: the first E+1 members (outside the window) are the
-    // neighbours, in (distance, index) order.  Hits go to this thread's column
-    // of s_hit.  Two groups (eight ranks) per step, loaded together.
-    int found = valid ? 0 : E + 1;
+    // Walk the row in (distance, index) order: for each realization the first
+    // E+1 members (outside the window) are its neighbours, in order.  Hits go
+    // to this thread's column of s_hit, per realization; counts (8 bits per
+    // realization) counts them, act holds the realizations still short of E+1.
+    // Two groups (eight ranks) per step, loaded together.
+    uint32_t act = valid ? all : 0u, counts = 0u;
     const int64_t col = (int64_t)(valid ? pos : 0) * 4;
     auto member = [&](int x) -> uint32_t {
       return bytes ? (uint32_t)map[x] : ((mw[x >> 5] >> (x & 31)) & 1u);
     };
     uint32_t st_entries = 0;
-    for (int g = 0; __any_sync(kFull, found <= E && g < groups); g += 2) {
-      const bool w0 = found <= E && g < groups, w1 = found <= E && g + 1 < groups;
+    for (int g = 0; __any_sync(kFull, act != 0u && g < groups); g += 2) {
+      const bool w0 = act != 0u && g < groups, w1 = act != 0u && g + 1 < groups;
       if (kStats) st_entries += (w0 ? 4u : 0u) + (w1 ? 4u : 0u);
       int x[8];  // ranks 4g .. 4g+7 of this query's row (index 0 when not loaded)
       if (p.table_u16) {
-        const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u.table_off + col;
+        const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u0.table_off + col;
         const uint2 v0 = w0 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)g * 4 * n_m))
                             : make_uint2(0u, 0u);
         const uint2 v1 = w1 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)(g + 1) * 4 * n_m))
@@ -952,7 +966,7 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
         x[0] = v0.x & 0xffffu; x[1] = v0.x >> 16; x[2] = v0.y & 0xffffu; x[3] = v0.y >> 16;
         x[4] = v1.x & 0xffffu; x[5] = v1.x >> 16; x[6] = v1.y & 0xffffu; x[7] = v1.y >> 16;
       } else {
-        const int32_t* t32 = static_cast<const int32_t*>(p.table) + u.table_off + col;
+        const int32_t* t32 = static_cast<const int32_t*>(p.table) + u0.table_off + col;
         const int4 v0 = w0 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)g * 4 * n_m))
                            : make_int4(0, 0, 0, 0);
         const int4 v1 = w1 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)(g + 1) * 4 * n_m))
@@ -960,81 +974,96 @@ __device__ void process_table_item(const KnnParams& p, const UnitDesc& u, int un
         x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
         x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
       }
-      // library members among the eight ranks, one bit each; then the members
-      // in rank order (most groups hold none)
+      // members among the eight ranks: bit 4c + b for rank c and realization b,
+      // so the set bits come in rank order (most steps hold none)
       uint32_t bits = 0u;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) bits |= member(x[c]) << c;
-      bits &= (w0 ? 0x0fu : 0u) | (w1 ? 0xf0u : 0u);
-      while (bits != 0u && found <= E) {
-        const int c = __ffs(bits) - 1;
+      for (int c = 0; c < 8; ++c) bits |= (member(x[c]) & act) << (4 * c);
+      bits &= (w0 ? 0x0000ffffu : 0u) | (w1 ? 0xffff0000u : 0u);
+      while (bits != 0u) {
+        const int pb = __ffs(bits) - 1;
         bits &= bits - 1u;
+        const int c = pb >> 2, b = pb & 3;
+        if (!((act >> b) & 1u)) continue;  // that realization completed at an earlier rank
         const int lo = (c & 1) ? x[1] : x[0], hi = (c & 1) ? x[3] : x[2];
         const int lo2 = (c & 1) ? x[5] : x[4], hi2 = (c & 1) ? x[7] : x[6];
         const int q4 = (c & 2) ? hi : lo, q4b = (c & 2) ? hi2 : lo2;
         const int xc = (c & 4) ? q4b : q4;
         if (abs(xc - m) > W) {
-          s_hit[found * kThreads + tid] = ((4 * g + c) << kHitRankShift) | xc;  // rank, index
-          ++found;
+          const int slot = (int)((counts >> (8 * b)) & 0xffu);
+          s_hit[(b * K + slot) * kThreads + tid] = ((4 * g + c) << kHitRankShift) | xc;  // rank, index
+          counts += 1u << (8 * b);
+          if (slot + 1 == K) act &= ~(1u << b);
         }
       }
     }
     if (kStats) {
       const uint32_t ent = __reduce_add_sync(kFull, st_entries);
       const unsigned vq = __popc(__ballot_sync(kFull, valid));
-      const unsigned fb = __popc(__ballot_sync(kFull, found <= E));
       if ((tid & 31) == 0) {
         atomicAdd(&p.stats[kStatTableEntries], (unsigned long long)ent);
-        atomicAdd(&p.stats[kStatTableQueries], (unsigned long long)vq);
-        atomicAdd(&p.stats[kStatTableFallbacks], (unsigned long long)fb);
+        atomicAdd(&p.stats[kStatTableQueries], (unsigned long long)vq * count);
       }
     }
-    int nb[E + 1];
-    float dd[E + 1];
-    if (found > E) {
-      // the neighbours' squared distances are read from the table (the same
-      // bits as recomputing them: the build used the same rounding sequence)
-#pragma unroll
-      for (int s2 = 0; s2 <= E; ++s2) {
-        const int h = valid ? s_hit[s2 * kThreads + tid] : 0;
-        const int rank = h >> kHitRankShift;
-        nb[s2] = h & ((1 << kHitRankShift) - 1);
-        dd[s2] = valid ? __ldg(p.table_d2 + u.table_off + (int64_t)(rank >> 2) * 4 * n_m + col +
-                               (rank & 3))
-                       : 0.f;
+    for (int b = 0; b < count; ++b) {
+      const int unit = unit0 + b;
+      const UnitDesc u = (b == 0) ? u0 : p.units[unit];
+      const bool full = ((counts >> (8 * b)) & 0xffu) >= (uint32_t)K;
+      if (kStats) {
+        const unsigned fb = __popc(__ballot_sync(kFull, valid && !full));
+        if ((tid & 31) == 0 && fb) atomicAdd(&p.stats[kStatTableFallbacks], (unsigned long long)fb);
       }
-    } else {
-      // Rare: fewer than E+1 members among the R nearest points; scan the
-      // library, keeping the E+1 smallest (distance, index) keys.
-      float kd[E + 1];
-      int kl[E + 1];
+      int nb[E + 1];
+      float dd[E + 1];
+      if (full || !valid) {
+        // the neighbours' squared distances are read from the table (the same
+        // bits as recomputing them: the build used the same rounding sequence)
 #pragma unroll
-      for (int s2 = 0; s2 <= E; ++s2) {
-        kd[s2] = INFINITY;
-        kl[s2] = INT_MAX;
-      }
-      for (int a = 0; a < L; ++a) {
-        const int l = lib[a];
-        if (abs(l - m) <= W) continue;
-        const float d = d2_point<E>(sj, off, tau, q, l);
-        if (key_less(d, l, kd[E], kl[E])) {
-          int s2 = E;
-          while (s2 > 0 && key_less(d, l, kd[s2 - 1], kl[s2 - 1])) {
-            kd[s2] = kd[s2 - 1];
-            kl[s2] = kl[s2 - 1];
-            --s2;
+        for (int s2 = 0; s2 <= E; ++s2) {
+          const int h = valid ? s_hit[(b * K + s2) * kThreads + tid] : 0;
+          const int rank = h >> kHitRankShift;
+          nb[s2] = h & ((1 << kHitRankShift) - 1);
+          dd[s2] = valid ? __ldg(p.table_d2 + u0.table_off + (int64_t)(rank >> 2) * 4 * n_m + col +
+                                 (rank & 3))
+                         : 0.f;
+        }
+      } else {
+        // Rare: fewer than E+1 members among the R nearest points; scan the
+        // library, keeping the E+1 smallest (distance, index) keys.
+        const int32_t* lib = p.lib + u.lib_off;
+        float q[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) q[e] = sj[m + off - e * tau];
+        float kd[E + 1];
+        int kl[E + 1];
+#pragma unroll
+        for (int s2 = 0; s2 <= E; ++s2) {
+          kd[s2] = INFINITY;
+          kl[s2] = INT_MAX;
+        }
+        for (int a = 0; a < L; ++a) {
+          const int l = lib[a];
+          if (abs(l - m) <= W) continue;
+          const float d = d2_point<E>(sj, off, tau, q, l);
+          if (key_less(d, l, kd[E], kl[E])) {
+            int s2 = E;
+            while (s2 > 0 && key_less(d, l, kd[s2 - 1], kl[s2 - 1])) {
+              kd[s2] = kd[s2 - 1];
+              kl[s2] = kl[s2 - 1];
+              --s2;
+            }
+            kd[s2] = d;
+            kl[s2] = l;
           }
-          kd[s2] = d;
-          kl[s2] = l;
+        }
+#pragma unroll
+        for (int s2 = 0; s2 <= E; ++s2) {
+          nb[s2] = kl[s2];
+          dd[s2] = kd[s2];
         }
       }
-#pragma unroll
-      for (int s2 = 0; s2 <= E; ++s2) {
-        nb[s2] = kl[s2];
-        dd[s2] = valid ? kd[s2] : 0.f;
-      }
+      finish_tile<E, false>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr);
     }
-    finish_tile<E, false>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr);
   }
 }
 
@@ -1056,11 +1085,12 @@ __global__ void __launch_bounds__(kThreads, 4) knn_table_kernel(KnnParams p) {
     if ((int64_t)it >= p.n_items) break;
     const WorkItem w = p.items[it];
     const UnitDesc u = p.units[w.unit];
-    if (u.E != E) {
+    if (u.E != E || w.count < 1 || w.count > kTableGroup ||
+        (w.count > 1 && u.n_m > kByteMapMax)) {
       if (threadIdx.x == 0) atomicOr(p.err, kErrBadUnit);
       continue;
     }
-    process_table_item<E, kStats>(p, u, w.unit, w.tile, smem, s_meta, ring_n);
+    process_table_item<E, kStats>(p, w.unit, w.count, w.tile, smem, s_meta, ring_n);
   }
   if (ring_n > 0) flush_ring(p, reinterpret_cast<const float*>(smem), s_meta, ring_n);
 }
@@ -1103,7 +1133,7 @@ size_t knn_table_smem(int max_nm) {
   const size_t bits = (size_t)((max_nm + 31) / 32) * 4;
   const size_t map = (max_nm <= kByteMapMax) ? (size_t)(max_nm + 3) / 4 * 4
                                              : (bits > (size_t)kByteMapMax ? bits : kByteMapMax);
-  return (size_t)kRingBytes + kHitBytes + map + 16;
+  return (size_t)kRingBytes + (size_t)kTableGroup * kHitBytes + map + 16;
 }
 
 #define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)

@@ -92,6 +92,7 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
        w += (int64_t)gridDim.x * blockDim.x) {
     items[w].unit = (int32_t)(w / per_unit);
     items[w].tile = (int32_t)((w % per_unit) * kBruteChunk);
+    items[w].count = 1;
   }
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < c.r;
        k += (int64_t)gridDim.x * blockDim.x) {

@@ -383,23 +383,33 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
               u.table_R = tab->second.second;
             }
             const int32_t uidx = (int32_t)ul->units.size();
-            for (int32_t q = 0; q < u.n_tiles; ++q) {
+            // Table realizations of one cell with a single target and a byte
+            // membership map are grouped kTableGroup at a time (consecutive k):
+            // the item of the group's first realization covers all of them.
+            const bool groupable = u.table_R > 0 && u.n_targets == 1 && u.n_m <= kTableGroupMaxNm;
+            const int32_t count =
+                groupable ? std::min<int32_t>(kTableGroup, pc.r - (k / kTableGroup) * kTableGroup) : 1;
+            const bool owns_items = !groupable || k % kTableGroup == 0;
+            for (int32_t q = 0; q < u.n_tiles && owns_items; ++q) {
               const int64_t nq = std::min<int64_t>(tileq, u.n_m - (int64_t)q * tileq);
               if (u.table_R > 0) {
-                // one item per kTableChunk tiles: one bitmap build, then per
-                // tile the expected table scan and the per-target epilogue
+                // one item per kTableChunk tiles: one membership map, then per
+                // tile one walk of each row (longer for a group: it ends when
+                // every realization has its E+1) and one epilogue per
+                // realization and target
                 if (q % kTableChunk == 0) {
-                  ul->items_table.push_back(WorkItem{uidx, q});
-                  ul->item_cost_table.push_back((double)L);
+                  ul->items_table.push_back(WorkItem{uidx, q, count});
+                  ul->item_cost_table.push_back((double)L * count);
                 }
-                ul->item_cost_table.back() += (double)nq * 12.0 * (E + 2) * (double)u.n_m /
-                                              (double)L + (double)u.n_targets * nq * 64.0;
+                ul->item_cost_table.back() +=
+                    (double)nq * 12.0 * (E + 2) * (double)u.n_m / (double)L * (1.0 + 0.1 * count) +
+                    (double)u.n_targets * nq * 64.0 * count;
               } else {
                 // one item per kBruteChunk tiles: one library staging (when it
                 // fits a shared-memory tile), then per tile the search and the
                 // per-target epilogue
                 if (q % kBruteChunk == 0) {
-                  ul->items.push_back(WorkItem{uidx, q});
+                  ul->items.push_back(WorkItem{uidx, q, 1});
                   ul->item_cost.push_back(64.0 * E * (double)L);
                 }
                 ul->item_cost.back() += (double)L * (double)nq * (2.0 * E + 1.0) +
