@@ -74,7 +74,7 @@ struct WorkItem {
   int32_t count;
 };
 constexpr int kBruteChunk = 8;         // query tiles per brute-force work item (one staging)
-constexpr int kTableGroup = 3;         // realizations per grouped table item, at most
+constexpr int kTableGroup = 4;         // realizations per grouped table item, at most
 constexpr int kTableGroupMaxNm = 32768;  // grouping needs a byte membership map (bit b: realization b)
 
 // Query order job: one per (job, library variable, E, tau).
