@@ -884,20 +884,20 @@ __device__ __forceinline__ float d2_point(const float* sj, int off, int tau, con
   return acc;
 }
 
-// Shared memory of the table kernel: the epilogue's ring of predictions, the hits
-// of every query for up to kTableGroup realizations (realization-major, then
-// slot-major, one column per thread), then the library
-// membership map: one byte per manifold point when the manifold has at most
-// kByteMapMax points (bit b: the point is in realization b's library; one load
-// per table entry), else one bit (one realization).
-constexpr int kHitBytes = (kMaxE + 1) * kThreads * 4;
+// Shared memory of the table kernel: the epilogue's ring of predictions, the
+// walk's records (below), then the library membership map: one byte per
+// manifold point when the manifold has at most kByteMapMax points (bit b: the
+// point is in realization b's library), else one bit (one realization).
+//
+// A record is one step of the walk (eight consecutive ranks of the row) that
+// held members of a realization: (step << 8) | flags, flag c marking rank
+// 8*step + c.  A realization stops recording once it has E+1 members, so it
+// keeps at most E+1 records: [kTableGroup][kMaxE+1][kThreads] 16-bit words.
+constexpr int kRecBytes = kTableGroup * (kMaxE + 1) * kThreads * 2;
 constexpr int kByteMapMax = 32768;
-// A hit is stored as (rank << kHitRankShift) | manifold index.
-constexpr int kHitRankShift = 20;
-static_assert(kTableMaxNm <= (1 << kHitRankShift), "manifold index must fit below the rank");
-static_assert(kTableMaxR <= (1 << (31 - kHitRankShift)), "rank must fit in the hit word");
+static_assert(kTableMaxR / 8 <= 256, "a record's step index has eight bits");
 static_assert(kTableGroupMaxNm <= kByteMapMax, "grouped table items need the byte map");
-static_assert(kTableGroup <= 4, "four bits per rank in the walk's member mask");
+static_assert(kTableGroup <= 4, "one byte of member flags per realization in 32 bits");
 
 template <int E, bool kStats>
 __device__ void process_table_item(const KnnParams& p, int unit0, int count, int tile0,
@@ -912,8 +912,8 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
   const int off = (E - 1) * tau;
   const float* sj = p.series + u0.series_off + (int64_t)u0.j * u0.n;
   float* s_ring = reinterpret_cast<float*>(smem);
-  int32_t* s_hit = reinterpret_cast<int32_t*>(smem + kRingBytes);  // [count][K][kThreads]
-  unsigned char* map = smem + kRingBytes + kTableGroup * kHitBytes;
+  uint16_t* s_rec = reinterpret_cast<uint16_t*>(smem + kRingBytes);  // [count][K][kThreads]
+  unsigned char* map = smem + kRingBytes + kRecBytes;
   const bool bytes = n_m <= kByteMapMax;
   const int words = bytes ? (n_m + 3) >> 2 : (n_m + 31) >> 5;  // 32-bit words of the map
   uint32_t* mw = reinterpret_cast<uint32_t*>(map);
@@ -936,22 +936,21 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
 
   const int tile1 = min(u0.n_tiles, tile0 + kTableChunk);
   const int groups = R >> 2;  // groups of four ranks
-  const uint32_t all = (1u << count) - 1u;
+  const uint32_t all = (count >= 4) ? 0xffffffffu : (1u << (8 * count)) - 1u;
+  const uint32_t table_limit = (uint32_t)(0x80 - K) * 0x01010101u;
   for (int tile = tile0; tile < tile1; ++tile) {
     const int pos = tile * kQT + tid;
     const bool valid = pos < n_m;
     const int m = p.order[u0.order_off + (valid ? pos : n_m - 1)];
 
-    // Walk the row in (distance, index) order: for each realization the first
-    // E+1 members (outside the window) are its neighbours, in order.  Hits go
-    // to this thread's column of s_hit, per realization; counts (8 bits per
-    // realization) counts them, act holds the realizations still short of E+1.
-    // Two groups (eight ranks) per step, loaded together.
-    uint32_t act = valid ? all : 0u, counts = 0u;
+    // Walk the row in (distance, index) order, eight ranks a step; for each
+    // realization the first E+1 members outside the window are its
+    // neighbours, in order.  Everything below works on four bytes at once,
+    // byte b for realization b: `flags` the step's members (bit c: rank
+    // 8*step + c), `counts` the members found so far, `act` 0xff while a
+    // realization still lacks some, `nrec` its records.
+    uint32_t act = valid ? all : 0u, counts = 0u, nrec = 0u;
     const int64_t col = (int64_t)(valid ? pos : 0) * 4;
-    auto member = [&](int x) -> uint32_t {
-      return bytes ? (uint32_t)map[x] : ((mw[x >> 5] >> (x & 31)) & 1u);
-    };
     uint32_t st_entries = 0;
     for (int g = 0; __any_sync(kFull, act != 0u && g < groups); g += 2) {
       const bool w0 = act != 0u && g < groups, w1 = act != 0u && g + 1 < groups;
@@ -974,27 +973,34 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
         x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
         x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
       }
-      // members among the eight ranks: bit 4c + b for rank c and realization b,
-      // so the set bits come in rank order (most steps hold none)
-      uint32_t bits = 0u;
+      // member flags: the map byte's bit b moved to bit c of byte b (the
+      // multiply spreads bits 0..3 to bits 0, 8, 16, 24); points inside the
+      // exclusion window |x - m| <= W are no members
+      uint32_t flags = 0u;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) bits |= (member(x[c]) & act) << (4 * c);
-      bits &= (w0 ? 0x0000ffffu : 0u) | (w1 ? 0xffff0000u : 0u);
-      while (bits != 0u) {
-        const int pb = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const int c = pb >> 2, b = pb & 3;
-        if (!((act >> b) & 1u)) continue;  // that realization completed at an earlier rank
-        const int lo = (c & 1) ? x[1] : x[0], hi = (c & 1) ? x[3] : x[2];
-        const int lo2 = (c & 1) ? x[5] : x[4], hi2 = (c & 1) ? x[7] : x[6];
-        const int q4 = (c & 2) ? hi : lo, q4b = (c & 2) ? hi2 : lo2;
-        const int xc = (c & 4) ? q4b : q4;
-        if (abs(xc - m) > W) {
-          const int slot = (int)((counts >> (8 * b)) & 0xffu);
-          s_hit[(b * K + slot) * kThreads + tid] = ((4 * g + c) << kHitRankShift) | xc;  // rank, index
-          counts += 1u << (8 * b);
-          if (slot + 1 == K) act &= ~(1u << b);
+      for (int c = 0; c < 8; ++c) {
+        uint32_t mb = bytes ? (uint32_t)map[x[c]] : ((mw[x[c] >> 5] >> (x[c] & 31)) & 1u);
+        mb = ((unsigned)x[c] - (unsigned)m + (unsigned)W <= 2u * (unsigned)W) ? 0u : mb;
+        flags |= ((mb * 0x00204081u) & 0x01010101u) << c;
+      }
+      flags &= act & ((w0 ? 0x0f0f0f0fu : 0u) | (w1 ? 0xf0f0f0f0u : 0u));
+      if (flags != 0u) {
+        // one record per realization with members in this step
+#pragma unroll
+        for (int b = 0; b < kTableGroup; ++b) {
+          const uint32_t fb = (flags >> (8 * b)) & 0xffu;
+          if (fb != 0u) {
+            const uint32_t i = (nrec >> (8 * b)) & 0xffu;  // < K: the realization was short
+            s_rec[(b * K + (int)i) * kThreads + tid] = (uint16_t)(((uint32_t)(g >> 1) << 8) | fb);
+            nrec += 1u << (8 * b);
+          }
         }
+        // per-byte population counts, then the realizations now complete
+        uint32_t v = flags - ((flags >> 1) & 0x55555555u);
+        v = (v & 0x33333333u) + ((v >> 2) & 0x33333333u);
+        counts += (v + (v >> 4)) & 0x0f0f0f0fu;  // each byte stays below K + 8
+        const uint32_t done = ((counts + table_limit) & 0x80808080u) >> 7;  // counts_b >= K
+        act &= ~(done * 0xffu);
       }
     }
     if (kStats) {
@@ -1016,16 +1022,26 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
       int nb[E + 1];
       float dd[E + 1];
       if (full || !valid) {
-        // the neighbours' squared distances are read from the table (the same
-        // bits as recomputing them: the build used the same rounding sequence)
+        // the first E+1 flagged ranks of the realization's records; their
+        // indices and squared distances are read from the table (the stored
+        // distances are the bits a recomputation would give: the build used
+        // the same rounding sequence)
+        const int nr = (int)((nrec >> (8 * b)) & 0xffu);
+        const uint16_t* rec = s_rec + b * K * kThreads + tid;
+        int ri = 0;
+        uint32_t cur = valid ? rec[0] : 0u;
 #pragma unroll
         for (int s2 = 0; s2 <= E; ++s2) {
-          const int h = valid ? s_hit[(b * K + s2) * kThreads + tid] : 0;
-          const int rank = h >> kHitRankShift;
-          nb[s2] = h & ((1 << kHitRankShift) - 1);
-          dd[s2] = valid ? __ldg(p.table_d2 + u0.table_off + (int64_t)(rank >> 2) * 4 * n_m + col +
-                                 (rank & 3))
-                         : 0.f;
+          while ((cur & 0xffu) == 0u && ri + 1 < nr) cur = rec[(++ri) * kThreads];
+          const uint32_t fl = cur & 0xffu;
+          const int c = fl ? __ffs(fl) - 1 : 0;  // fl > 0 whenever the walk was full
+          cur &= ~(1u << c);
+          const int rank = 8 * (int)(cur >> 8) + c;
+          const int64_t at = u0.table_off + (int64_t)(rank >> 2) * 4 * n_m + col + (rank & 3);
+          nb[s2] = !valid ? 0
+                          : (p.table_u16 ? (int)__ldg(static_cast<const uint16_t*>(p.table) + at)
+                                         : __ldg(static_cast<const int32_t*>(p.table) + at));
+          dd[s2] = valid ? __ldg(p.table_d2 + at) : 0.f;
         }
       } else {
         // Rare: fewer than E+1 members among the R nearest points; scan the
@@ -1133,7 +1149,7 @@ size_t knn_table_smem(int max_nm) {
   const size_t bits = (size_t)((max_nm + 31) / 32) * 4;
   const size_t map = (max_nm <= kByteMapMax) ? (size_t)(max_nm + 3) / 4 * 4
                                              : (bits > (size_t)kByteMapMax ? bits : kByteMapMax);
-  return (size_t)kRingBytes + (size_t)kTableGroup * kHitBytes + map + 16;
+  return (size_t)kRingBytes + (size_t)kRecBytes + map + 16;
 }
 
 #define CCM_FOR_E(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
