@@ -74,10 +74,11 @@ typedef enum {
                                       per-(variable, E, tau) tables built in the same run,
                                       where that is faster and the tables fit a quarter of
                                       the context budget; results are identical either way.
-                                      Tuning knobs (environment): CCM_TABLE_SAFETY (read at
-                                      each ccm_plan; default 4: table row length over the
-                                      expected scan length) and CCM_TABLE_CROSSOVER (read
-                                      once; default 190: tables for L >= sqrt(c*N_m/(E+1))) */
+                                      Tuning knobs (environment, read at each ccm_plan):
+                                      CCM_TABLE_SAFETY (default 2: table row length over the
+                                      expected scan length), CCM_TABLE_CROSSOVER (default
+                                      40) and CCM_TABLE_FLOOR (default 256): tables for
+                                      L >= max(floor, sqrt(c*N_m/(E+1))) */
 #define CCM_SEARCH_STATS     0x20u /* the neighbour-search kernels also count their work
                                       (ccm_plan_search_stats); a separately compiled
                                       counting variant, slower, same results */

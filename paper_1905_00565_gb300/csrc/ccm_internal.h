@@ -122,7 +122,7 @@ struct KnnParams {
   const int32_t* lib;
   const int32_t* order;   // query order (manifold index per position)
   const void* table;      // distance indexing tables (units with table_R > 0)
-  const float* table_d2;  // the FP32 squared distance of every table entry, same layout
+  const float* table_dist;  // every table entry's distance sqrt_hw(FP32 squared distance), same layout
   int32_t table_u16;      // 1: uint16 entries (every manifold below 65536 points), 0: int32
   double* partials;       // 6 doubles per query tile
   const double* obs;      // observed-moment tile records (TargetDesc::obs_tile)
@@ -169,10 +169,13 @@ __device__ __forceinline__ float sqrt_hw(float x) {
   asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float simplex_u(float d2, float d1, float inv_d1, float wfloor) {
-  const float d = sqrt_hw(d2);
+// The same from the distance d = sqrt_hw(d2) itself.
+__device__ __forceinline__ float simplex_u_dist(float d, float d1, float inv_d1, float wfloor) {
   const float u = (d1 > 0.f) ? __expf(-__fmul_rn(d, inv_d1)) : ((d == 0.f) ? 1.f : 0.f);
   return fmaxf(u, wfloor);
+}
+__device__ __forceinline__ float simplex_u(float d2, float d1, float inv_d1, float wfloor) {
+  return simplex_u_dist(sqrt_hw(d2), d1, inv_d1, wfloor);
 }
 
 // Error flag values written by kernels.
@@ -196,7 +199,7 @@ cudaError_t table_prepare();
 // One launch builds the tables of jobs[0..n_jobs), all of embedding dimension E.
 cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs, int E,
                                int max_nm, int max_R, const int32_t* order, void* table,
-                               float* table_d2, int table_u16, cudaStream_t s);
+                               float* table_dist, int table_u16, cudaStream_t s);
 
 // Fused kernel (knn_fused.cu).
 int knn_block_threads();

@@ -385,8 +385,9 @@ __device__ __forceinline__ void flush_ring(const KnnParams& p, const float* ring
 }
 
 // Everything after the neighbour search, shared by the brute-force and the
-// table paths: dd[0..E] ascending FP32 squared distances and nb[0..E] the
-// neighbours of query m (itself excluded).  Simplex weights and the
+// table paths: dd[0..E] ascending FP32 squared distances (kDist: their
+// distances sqrt_hw(d2) already) and nb[0..E] the neighbours of query m
+// (itself excluded).  Simplex weights and the
 // prediction of every target; each target's prediction vector goes to the
 // next ring slot (ring_n, the same in every thread), and a full ring is
 // reduced (flush_ring).  The CTA flushes what is left when it runs out of
@@ -398,7 +399,7 @@ __device__ __forceinline__ void flush_ring(const KnnParams& p, const float* ring
 // be searching, so nothing else of the buffer is touched.  kKeep false: they
 // stay in registers.
 static_assert(kMaxE + 1 <= kBuf, "the epilogue keeps E+1 entries in a candidate column");
-template <int E, bool kKeep>
+template <int E, bool kKeep, bool kDist = false>
 __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& u, int unit,
                                             int tile, int m, bool valid, const float (&dd)[E + 1],
                                             const int (&nb)[E + 1], float* ring, RingMeta* meta,
@@ -412,14 +413,14 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   // hardware approximation that is the same everywhere), so the brute-force
   // and table kernels, the plain comparator and every batch produce the same
   // bits.
-  const float d1 = sqrt_hw(dd[0]);
+  const float d1 = kDist ? dd[0] : sqrt_hw(dd[0]);
   const float inv_d1 = (d1 > 0.f) ? __frcp_rn(d1) : 0.f;
   float w[E + 1];
   int nbc[E + 1];
   float usum = 0.f;
 #pragma unroll
   for (int s = 0; s <= E; ++s) {
-    w[s] = simplex_u(dd[s], d1, inv_d1, u.wfloor);
+    w[s] = kDist ? simplex_u_dist(dd[s], d1, inv_d1, u.wfloor) : simplex_u(dd[s], d1, inv_d1, u.wfloor);
     usum = __fadd_rn(usum, w[s]);
     // an unfilled slot (only possible with non-finite device input) reads, and
     // is reported, in bounds
@@ -867,8 +868,8 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
 // --------------------------------------------------------------------------
 // Table path: the library's members are marked in a shared-memory bitmap and
 // each query walks its row of the distance indexing table (sorted by (FP32
-// squared distance, index) over the whole manifold) until it has met E+1
-// library members other than itself.  Those are, in order, the E+1 nearest
+// squared distance, index) over the whole manifold, the query itself left
+// out) until it has met E+1 library members outside the exclusion window.  Those are, in order, the E+1 nearest
 // library neighbours -- the same list the brute-force scan produces.  A query
 // whose R table entries hold fewer members falls back to scanning the library.
 template <int E>
@@ -943,9 +944,9 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
     const bool valid = pos < n_m;
     const int m = p.order[u0.order_off + (valid ? pos : n_m - 1)];
 
-    // Walk the row in (distance, index) order, eight ranks a step; for each
-    // realization the first E+1 members outside the window are its
-    // neighbours, in order.  Everything below works on four bytes at once,
+    // Walk the row (every manifold point but m, in (distance, index) order),
+    // eight ranks a step; for each realization the first E+1 members outside
+    // the window are its neighbours, in order.  Everything below works on four bytes at once,
     // byte b for realization b: `flags` the step's members (bit c: rank
     // 8*step + c), `counts` the members found so far, `act` 0xff while a
     // realization still lacks some, `nrec` its records.
@@ -974,16 +975,23 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
         x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
       }
       // member flags: the map byte's bit b moved to bit c of byte b (the
-      // multiply spreads bits 0..3 to bits 0, 8, 16, 24); points inside the
-      // exclusion window |x - m| <= W are no members
+      // multiply spreads bits 0..3 to bits 0, 8, 16, 24)
       uint32_t flags = 0u;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        uint32_t mb = bytes ? (uint32_t)map[x[c]] : ((mw[x[c] >> 5] >> (x[c] & 31)) & 1u);
-        mb = ((unsigned)x[c] - (unsigned)m + (unsigned)W <= 2u * (unsigned)W) ? 0u : mb;
+        const uint32_t mb = bytes ? (uint32_t)map[x[c]] : ((mw[x[c] >> 5] >> (x[c] & 31)) & 1u);
         flags |= ((mb * 0x00204081u) & 0x01010101u) << c;
       }
       flags &= act & ((w0 ? 0x0f0f0f0fu : 0u) | (w1 ? 0xf0f0f0f0u : 0u));
+      if (W > 0) {
+        // points inside the exclusion window |x - m| <= W are no neighbours
+        // (the row never holds m itself, so W = 0 excludes nothing)
+        uint32_t win = 0u;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          win |= (((unsigned)x[c] - (unsigned)m + (unsigned)W <= 2u * (unsigned)W) ? 1u : 0u) << c;
+        flags &= ~(win * 0x01010101u);
+      }
       if (flags != 0u) {
         // one record per realization with members in this step
 #pragma unroll
@@ -1023,9 +1031,9 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
       float dd[E + 1];
       if (full || !valid) {
         // the first E+1 flagged ranks of the realization's records; their
-        // indices and squared distances are read from the table (the stored
-        // distances are the bits a recomputation would give: the build used
-        // the same rounding sequence)
+        // indices and distances are read from the table (the stored distances
+        // are the bits the epilogue would compute: the build used the same
+        // rounding sequence and the same square root)
         const int nr = (int)((nrec >> (8 * b)) & 0xffu);
         const uint16_t* rec = s_rec + b * K * kThreads + tid;
         int ri = 0;
@@ -1041,7 +1049,7 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
           nb[s2] = !valid ? 0
                           : (p.table_u16 ? (int)__ldg(static_cast<const uint16_t*>(p.table) + at)
                                          : __ldg(static_cast<const int32_t*>(p.table) + at));
-          dd[s2] = valid ? __ldg(p.table_d2 + at) : 0.f;
+          dd[s2] = valid ? __ldg(p.table_dist + at) : 0.f;  // a distance, not squared
         }
       } else {
         // Rare: fewer than E+1 members among the R nearest points; scan the
@@ -1075,10 +1083,10 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
 #pragma unroll
         for (int s2 = 0; s2 <= E; ++s2) {
           nb[s2] = kl[s2];
-          dd[s2] = kd[s2];
+          dd[s2] = sqrt_hw(kd[s2]);
         }
       }
-      finish_tile<E, false>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr);
+      finish_tile<E, false, true>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr);
     }
   }
 }

@@ -185,20 +185,33 @@ struct UnitList {
   double pairs = 0.0, flops = 0.0;    // neighbour-search work actually done
 };
 
+// Table tunables: the crossover constant c and the floor of table_min_L, and
+// the safety factor s of R over the expected scan length (see below).  The
+// environment variables CCM_TABLE_CROSSOVER, CCM_TABLE_FLOOR and
+// CCM_TABLE_SAFETY replace the defaults (read at each ccm_plan; tuning and
+// measurement only).
+struct TableTuning {
+  double crossover, floor, safety;
+};
+TableTuning read_table_tuning() {
+  TableTuning r{40.0, 256.0, 2.0};
+  if (const char* e = getenv("CCM_TABLE_CROSSOVER")) r.crossover = std::max(0.0, atof(e));
+  if (const char* e = getenv("CCM_TABLE_FLOOR")) r.floor = std::max(16.0, atof(e));
+  if (const char* e = getenv("CCM_TABLE_SAFETY")) r.safety = std::max(0.01, atof(e));
+  return r;
+}
+
 // Smallest L whose realizations read a distance indexing table.  A table
 // scan visits about (E+1)*N_m/L rows per query; brute force (with chunk
 // pruning) costs about L distance evaluations of E coordinates per query.
-// Measured on GB300 (N_m = 10^4) the two break even near L = 900 for E = 1
-// and L = 450 for E = 10, i.e. L ~ sqrt(190*N_m/(E+1)); below that brute
-// force is faster.  The last term keeps R = 4(E+2)N_m/L + 64 within kTableMaxR.
-// CCM_TABLE_CROSSOVER replaces the 190 (tuning and measurement only).
-double table_min_L(int32_t E, int64_t n_m) {
-  static const double c = [] {
-    const char* env = getenv("CCM_TABLE_CROSSOVER");
-    return env ? std::max(0.0, atof(env)) : 190.0;
-  }();
-  return std::max({256.0, std::ceil(std::sqrt(c * (double)n_m / (double)(E + 1))),
-                   std::ceil(4.0 * (E + 2) * (double)n_m / (double)(kTableMaxR - 64))});
+// Measured on GB300 (N_m = 10^4, the table build included) the sweep is
+// fastest with c = 40, a floor of 256 and s = 2: L ~ sqrt(c*N_m/(E+1)) is where
+// a grouped table walk overtakes brute force; the floor keeps R, and with it
+// the build's sorts, short.  The last term keeps R = s(E+2)N_m/L + 64 within
+// kTableMaxR.
+double table_min_L(int32_t E, int64_t n_m, const TableTuning& t) {
+  return std::max({t.floor, std::ceil(std::sqrt(t.crossover * (double)n_m / (double)(E + 1))),
+                   std::ceil(t.safety * (E + 2) * (double)n_m / (double)(kTableMaxR - 64))});
 }
 
 // Append the units of one problem.  Offsets: series block, first rho index.
@@ -285,18 +298,17 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         }
   // Distance indexing tables (unless CCM_NO_TABLE): per (j, E, tau),
   // realizations with L >= table_min_L read their neighbours from a table of
-  // the R nearest points of every query; R covers about four times the
-  // expected scan length (E+2)*N_m/L at the smallest such L
-  // (CCM_TABLE_SAFETY changes the four).  A table is built only when the
+  // the R nearest points of every query; R covers s times the expected
+  // scan length (E+2)*N_m/L at the smallest such L.  A table is built only when the
   // realizations that use it would otherwise scan at least 8*N_m library
   // points in total (its build costs about N_m^2 distance evaluations), and
   // while the plan's tables stay within table_cap_bytes; the realizations of
   // a (j, E, tau) without a table use brute force.
   std::map<std::tuple<int32_t, int32_t, int32_t>, std::pair<int64_t, int32_t>> table_of;
-  // Safety factor of R over the expected scan length; CCM_TABLE_SAFETY trades
-  // table memory for how often a query falls back to scanning its library.
-  double safety = 4.0;
-  if (const char* env = getenv("CCM_TABLE_SAFETY")) safety = std::max(0.01, atof(env));
+  // Safety factor of R over the expected scan length: table memory and build
+  // time against how often a query falls back to scanning its library.
+  const TableTuning tt = read_table_tuning();
+  const double safety = tt.safety;
   double table_bytes = 0.0;
   if (!(pc.flags & CCM_NO_TABLE)) {
     for (int32_t j : lib_vars)
@@ -304,7 +316,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         for (int32_t tau : pc.tau) {
           const int64_t n_m = pc.n - (int64_t)(E - 1) * tau;
           if (n_m > kTableMaxNm) continue;
-          const double ls = table_min_L(E, n_m);
+          const double ls = table_min_L(E, n_m, tt);
           int64_t lmin = -1;
           double lsum = 0.0;
           for (int64_t L : pc.L)
@@ -316,8 +328,10 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
           // the window removes up to 2W more of the nearest points from every row
           int64_t R = (int64_t)std::ceil(safety * (E + 2) * (double)n_m / (double)lmin) + 64 +
                       2 * (int64_t)pc.theiler;
-          // whole groups of four ranks (the table's layout)
-          R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR), n_m / 4 * 4);
+          // whole groups of four ranks (the table's layout), from the n_m - 1
+          // points other than the query
+          R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR),
+                                (n_m - 1) / 4 * 4);
           // indices (2 or 4 bytes) and FP32 squared distances
           const double bytes = (double)n_m * (double)R * ((n_m < 65536 ? 2.0 : 4.0) + 4.0);
           if (table_bytes + bytes > table_cap_bytes) continue;
@@ -378,7 +392,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
               ul->targets.push_back(tg);
             }
             const auto tab = table_of.find(std::make_tuple(j, E, tau));
-            if (tab != table_of.end() && (double)L >= table_min_L(E, u.n_m)) {
+            if (tab != table_of.end() && (double)L >= table_min_L(E, u.n_m, tt)) {
               u.table_off = tab->second.first;
               u.table_R = tab->second.second;
             }
@@ -504,7 +518,7 @@ void sort_items(UnitList* ul) {
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
          counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
-         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_d2 = 0, stats = 0,
+         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_dist = 0, stats = 0,
          total = 0;
 };
 
@@ -531,7 +545,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.orders = take(sizeof(OrderJob) * ul.orders.size());
   a.targets = take(sizeof(TargetDesc) * ul.targets.size());
   a.table = take(ul.table_elem() * (size_t)ul.table_total);
-  a.table_d2 = take(sizeof(float) * (size_t)ul.table_total);
+  a.table_dist = take(sizeof(float) * (size_t)ul.table_total);
   a.tables = take(sizeof(TableJob) * ul.tables.size());
   a.items_table = take(sizeof(WorkItem) * ul.items_table.size());
   a.obs = take(sizeof(double) * kObsStride * (size_t)ul.obs_total);
@@ -697,7 +711,7 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.lib = reinterpret_cast<const int32_t*>(base + ar.lib);
   kp.order = reinterpret_cast<const int32_t*>(base + ar.order);
   kp.table = base + ar.table;
-  kp.table_d2 = reinterpret_cast<const float*>(base + ar.table_d2);
+  kp.table_dist = reinterpret_cast<const float*>(base + ar.table_dist);
   kp.table_u16 = ul.table_u16();
   kp.partials = reinterpret_cast<double*>(base + ar.part);
   kp.obs = reinterpret_cast<const double*>(base + ar.obs);
@@ -761,7 +775,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                                 reinterpret_cast<const TableJob*>(base + ar.tables) + g0,
                                 (int64_t)(g1 - g0), te, nm, rmax,
                                 reinterpret_cast<const int32_t*>(base + ar.order),
-                                base + ar.table, reinterpret_cast<float*>(base + ar.table_d2),
+                                base + ar.table, reinterpret_cast<float*>(base + ar.table_dist),
                                 ul.table_u16(), s));
     g0 = g1;
   }

@@ -6,20 +6,22 @@
 //
 // For one (library variable, E, tau) the table holds, for every query
 // position pos of the query order, the R nearest manifold points of the query
-// order[pos] over the WHOLE manifold, sorted by (FP32 squared distance, index),
-// the same key the brute-force selection uses.  For a realization whose library
-// is a subset of the manifold, the first E+1 table entries that are library
-// members (the query itself skipped) are exactly its E+1 nearest library
-// neighbours: restricting a total order to a subset keeps its order.
+// m = order[pos] over the WHOLE manifold, m itself left out (no neighbour
+// list holds it), sorted by (FP32 squared distance, index), the same key the
+// brute-force selection uses.  For a realization whose library is a subset of
+// the manifold, the first E+1 table entries that are library members (outside
+// the exclusion window) are exactly its E+1 nearest library neighbours:
+// restricting a total order to a subset keeps its order.
 //
 // Layout: ranks in groups of four, table[table_off + (r/4) * 4*n_m + pos*4 +
 // r%4], so that one 8-byte (16-bit entries) or 16-byte (32-bit) load gives a
 // query four consecutive ranks and the 32 consecutive query positions of a
 // warp read one group with one coalesced access; 16-bit entries when every
 // manifold of the plan has fewer than 65536 points, else 32-bit.  A float
-// array of the same layout holds each entry's squared distance, so that the
-// scan reads the E+1 distances it needs instead of recomputing them from E
-// scattered coordinates each.
+// array of the same layout holds each entry's distance (the square root the
+// simplex weights take of the FP32 squared distance, computed the same way),
+// so that the scan reads the E+1 distances it needs instead of recomputing
+// them from E scattered coordinates each.
 //
 // Build: one warp per query position, one kernel per E (its registers follow
 // that E).  A histogram of the top 11 bits of the
@@ -144,7 +146,7 @@ __device__ __forceinline__ uint32_t d2_bits_staged(const float* stage, int off, 
 // series values, or null.
 template <int E>
 __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
-                          const int32_t* order, void* table, float* table_d2, int u16,
+                          const int32_t* order, void* table, float* table_dist, int u16,
                           uint32_t* hist, unsigned long long* keys, unsigned long long* bnd,
                           uint32_t* cnt, int region_keys, float* stage) {
   const int lane = threadIdx.x & 31;
@@ -234,7 +236,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
-              if (bits[u] <= T && x0 + 32 * u < len) {
+              if (bits[u] <= T && x0 + 32 * u < len && base + x0 + 32 * u != m) {
                 const uint32_t at = atomicAdd(&cnt[0], 1u);
                 if (at < (uint32_t)C) keys[at] = key_of(bits[u], base + x0 + 32 * u);
               }
@@ -252,7 +254,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
       }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        if (bits[u] <= T && x0 + 32 * u < n_m) {
+        if (bits[u] <= T && x0 + 32 * u < n_m && x0 + 32 * u != m) {
           const uint32_t at = atomicAdd(&cnt[0], 1u);
           if (at < (uint32_t)C) keys[at] = key_of(bits[u], x0 + 32 * u);
         }
@@ -279,6 +281,9 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
   __syncwarp();
   for (int x = lane; x < n_m; x += 32) atomicAdd(&hist[d2_bits<E>(s, off, tau, q, x) >> 21], 1u);
   __syncwarp();
+  // m itself was counted: its squared distance is exactly 0 (bin 0)
+  if (lane == 0) hist[0] -= 1u;
+  __syncwarp();
   int b1;
   uint32_t below1, in_b1;
   select_bin(hist, 2048, R, &b1, &below1, &in_b1);
@@ -294,7 +299,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
     __syncwarp();
     for (int x = lane; x < n_m; x += 32) {
       const uint32_t bits = d2_bits<E>(s, off, tau, q, x);
-      const uint32_t bin = bits >> 21;
+      const uint32_t bin = (x != m) ? bits >> 21 : 0xffffffffu;
       if (bin < (uint32_t)b1) keys[atomicAdd(&cnt[0], 1u)] = key_of(bits, x);
       else if (bin == (uint32_t)b1) bnd[atomicAdd(&cnt[1], 1u)] = key_of(bits, x);
     }
@@ -330,6 +335,8 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
         if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> sh) & dm], 1u);
       }
       __syncwarp();
+      if (lane == 0 && prefix == 0u) hist[0] -= 1u;  // m itself (bits 0) was counted
+      __syncwarp();
       int bin;
       uint32_t before, cnt;
       select_bin(hist, nbins, rank, &bin, &before, &cnt);
@@ -345,8 +352,8 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
     for (int base = 0; base < n_m; base += 32) {
       const int x = base + lane;
       const uint32_t bits = (x < n_m) ? d2_bits<E>(s, off, tau, q, x) : 0xffffffffu;
-      const bool less = (x < n_m) && bits < T;
-      const bool tie = (x < n_m) && bits == T;
+      const bool less = (x < n_m) && x != m && bits < T;
+      const bool tie = (x < n_m) && x != m && bits == T;
       const unsigned lm = __ballot_sync(kFullMask, less);
       const unsigned tm = __ballot_sync(kFullMask, tie);
       if (less) keys[less_seen + __popc(lm & below_lane)] = key_of(bits, x);
@@ -364,8 +371,9 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
   }
   __syncwarp();
   const int64_t base = jb.table_off + (int64_t)pos * 4;
-  for (int r = lane; r < R; r += 32)  // each entry's squared distance, beside it
-    table_d2[base + (int64_t)(r >> 2) * 4 * n_m + (r & 3)] = __uint_as_float((uint32_t)(keys[r] >> 32));
+  for (int r = lane; r < R; r += 32)  // each entry's distance (the epilogue's square root), beside it
+    table_dist[base + (int64_t)(r >> 2) * 4 * n_m + (r & 3)] =
+        sqrt_hw(__uint_as_float((uint32_t)(keys[r] >> 32)));
   if (u16) {
     uint16_t* out = static_cast<uint16_t*>(table) + base;
     for (int r = lane; r < R; r += 32)
@@ -381,7 +389,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
 template <int E>
 __global__ void __launch_bounds__(kTableWarps * 32, 2)
 table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
-                   float* table_d2, int u16, int rcap, int staged) {
+                   float* table_dist, int u16, int rcap, int staged) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_cnt[kTableWarps][2];  // per warp: entries below b1, entries of b1
   const TableJob jb = jobs[blockIdx.y];
@@ -401,7 +409,7 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
   float* stage = (staged && (E - 1) * jb.tau <= kStageHalo)
                      ? reinterpret_cast<float*>(smem + kTableWarps * table_warp_bytes(rcap))
                      : nullptr;
-  build_row<E>(s, jb, pos, pos < jb.n_m, order, table, table_d2, u16, hist, keys, bnd,
+  build_row<E>(s, jb, pos, pos < jb.n_m, order, table, table_dist, u16, hist, keys, bnd,
                s_cnt[warp], (int)(table_warp_bytes(rcap) / 8), stage);
 }
 
@@ -429,7 +437,7 @@ cudaError_t table_prepare() {
 
 cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs, int E,
                                int max_nm, int max_R, const int32_t* order, void* table,
-                               float* table_d2, int table_u16, cudaStream_t s) {
+                               float* table_dist, int table_u16, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
   int rcap = 32;
   while (rcap < max_R) rcap <<= 1;
@@ -439,7 +447,7 @@ cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_
 #define CCM_TBLAUNCH(EV)                                                                 \
   if (E == EV) {                                                                         \
     table_build_kernel<EV><<<grid, kTableWarps * 32, table_smem(rcap, staged), s>>>(     \
-        series, jobs, order, table, table_d2, table_u16, rcap, staged);                  \
+        series, jobs, order, table, table_dist, table_u16, rcap, staged);                  \
     return cudaGetLastError();                                                           \
   }
   CCM_FOR_E(CCM_TBLAUNCH)
