@@ -104,20 +104,20 @@ __device__ __forceinline__ void select_bin(const uint32_t* hist, int nbins, int 
   *count_out = __shfl_sync(kFullMask, count, owner);
 }
 
-// Ascending bitonic sort of n (a power of two) keys by one warp.
+// Ascending bitonic sort of n (a power of two, >= 32) keys by one warp.  Each
+// stage has n/2 compare-exchange pairs (i, i + jj), i the t-th index with bit
+// jj clear: every lane takes whole pairs.
 __device__ __forceinline__ void warp_bitonic(unsigned long long* keys, int n) {
   const int lane = threadIdx.x & 31;
+  const int half = n >> 1;
   for (int k = 2; k <= n; k <<= 1) {
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int i = lane; i < n; i += 32) {
-        const int ixj = i ^ jj;
-        if (ixj > i) {
-          const unsigned long long a = keys[i], b = keys[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            keys[i] = b;
-            keys[ixj] = a;
-          }
+      for (int t = lane; t < half; t += 32) {
+        const int i = 2 * t - (t & (jj - 1));
+        const unsigned long long a = keys[i], b = keys[i + jj];
+        if ((a > b) == ((i & k) == 0)) {
+          keys[i] = b;
+          keys[i + jj] = a;
         }
       }
       __syncwarp();
