@@ -77,7 +77,7 @@ typedef enum {
                                       Tuning knobs (environment, read at each ccm_plan):
                                       CCM_TABLE_SAFETY (default 2: table row length over the
                                       expected scan length), CCM_TABLE_CROSSOVER (default
-                                      40) and CCM_TABLE_FLOOR (default 256): tables for
+                                      20) and CCM_TABLE_FLOOR (default 256): tables for
                                       L >= max(floor, sqrt(c*N_m/(E+1))) */
 #define CCM_SEARCH_STATS     0x20u /* the neighbour-search kernels also count their work
                                       (ccm_plan_search_stats); a separately compiled

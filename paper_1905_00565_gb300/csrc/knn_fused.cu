@@ -900,6 +900,78 @@ static_assert(kTableMaxR / 8 <= 256, "a record's step index has eight bits");
 static_assert(kTableGroupMaxNm <= kByteMapMax, "grouped table items need the byte map");
 static_assert(kTableGroup <= 4, "one byte of member flags per realization in 32 bits");
 
+// One query's walk along its table row (see process_table_item): `at` is the
+// element of its rank group 0, `rec` its column of the records, and act,
+// counts and nrec the per-realization bytes described there.  The map is a
+// byte map (kBytes) or a bitmap, fixed per work item, so each kind gets its
+// own loop.
+template <int K, bool kBytes, bool kStats>
+__device__ __forceinline__ void table_walk(const KnnParams& p, int64_t at, int n_m, int groups, int m,
+                                           int W, const unsigned char* map, uint16_t* rec,
+                                           uint32_t& act, uint32_t& counts, uint32_t& nrec,
+                                           uint32_t& st_entries) {
+  const uint32_t table_limit = (uint32_t)(0x80 - K) * 0x01010101u;
+  for (int g = 0; __any_sync(kFull, act != 0u && g < groups); g += 2) {
+    const bool w0 = act != 0u && g < groups, w1 = act != 0u && g + 1 < groups;
+    if (kStats) st_entries += (w0 ? 4u : 0u) + (w1 ? 4u : 0u);
+    int x[8];  // ranks 4g .. 4g+7 of this query's row (index 0 when not loaded)
+    if (p.table_u16) {
+      const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + at;
+      const uint2 v0 = w0 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)g * 4 * n_m))
+                          : make_uint2(0u, 0u);
+      const uint2 v1 = w1 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)(g + 1) * 4 * n_m))
+                          : make_uint2(0u, 0u);
+      x[0] = v0.x & 0xffffu; x[1] = v0.x >> 16; x[2] = v0.y & 0xffffu; x[3] = v0.y >> 16;
+      x[4] = v1.x & 0xffffu; x[5] = v1.x >> 16; x[6] = v1.y & 0xffffu; x[7] = v1.y >> 16;
+    } else {
+      const int32_t* t32 = static_cast<const int32_t*>(p.table) + at;
+      const int4 v0 = w0 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)g * 4 * n_m))
+                         : make_int4(0, 0, 0, 0);
+      const int4 v1 = w1 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)(g + 1) * 4 * n_m))
+                         : make_int4(0, 0, 0, 0);
+      x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+      x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+    }
+    // member flags: the map byte's bit b moved to bit c of byte b (the
+    // multiply spreads bits 0..3 to bits 0, 8, 16, 24)
+    uint32_t flags = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t mb = kBytes ? (uint32_t)map[x[c]]
+                                 : ((reinterpret_cast<const uint32_t*>(map)[x[c] >> 5] >> (x[c] & 31)) & 1u);
+      flags |= (kBytes ? ((mb * 0x00204081u) & 0x01010101u) : mb) << c;  // a bitmap: one realization
+    }
+    flags &= act & ((w0 ? 0x0f0f0f0fu : 0u) | (w1 ? 0xf0f0f0f0u : 0u));
+    if (W > 0) {
+      // points inside the exclusion window |x - m| <= W are no neighbours
+      // (the row never holds m itself, so W = 0 excludes nothing)
+      uint32_t win = 0u;
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        win |= (((unsigned)x[c] - (unsigned)m + (unsigned)W <= 2u * (unsigned)W) ? 1u : 0u) << c;
+      flags &= ~(win * 0x01010101u);
+    }
+    if (flags != 0u) {
+      // one record per realization with members in this step
+#pragma unroll
+      for (int b = 0; b < kTableGroup; ++b) {
+        const uint32_t fb = (flags >> (8 * b)) & 0xffu;
+        if (fb != 0u) {
+          const uint32_t i = (nrec >> (8 * b)) & 0xffu;  // < K: the realization was short
+          rec[(b * K + (int)i) * kThreads] = (uint16_t)(((uint32_t)(g >> 1) << 8) | fb);
+          nrec += 1u << (8 * b);
+        }
+      }
+      // per-byte population counts, then the realizations now complete
+      uint32_t v = flags - ((flags >> 1) & 0x55555555u);
+      v = (v & 0x33333333u) + ((v >> 2) & 0x33333333u);
+      counts += (v + (v >> 4)) & 0x0f0f0f0fu;  // each byte stays below K + 8
+      const uint32_t done = ((counts + table_limit) & 0x80808080u) >> 7;  // counts_b >= K
+      act &= ~(done * 0xffu);
+    }
+  }
+}
+
 template <int E, bool kStats>
 __device__ void process_table_item(const KnnParams& p, int unit0, int count, int tile0,
                                    unsigned char* smem, RingMeta* meta, int& ring_n) {
@@ -938,7 +1010,6 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
   const int tile1 = min(u0.n_tiles, tile0 + kTableChunk);
   const int groups = R >> 2;  // groups of four ranks
   const uint32_t all = (count >= 4) ? 0xffffffffu : (1u << (8 * count)) - 1u;
-  const uint32_t table_limit = (uint32_t)(0x80 - K) * 0x01010101u;
   for (int tile = tile0; tile < tile1; ++tile) {
     const int pos = tile * kQT + tid;
     const bool valid = pos < n_m;
@@ -953,64 +1024,12 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
     uint32_t act = valid ? all : 0u, counts = 0u, nrec = 0u;
     const int64_t col = (int64_t)(valid ? pos : 0) * 4;
     uint32_t st_entries = 0;
-    for (int g = 0; __any_sync(kFull, act != 0u && g < groups); g += 2) {
-      const bool w0 = act != 0u && g < groups, w1 = act != 0u && g + 1 < groups;
-      if (kStats) st_entries += (w0 ? 4u : 0u) + (w1 ? 4u : 0u);
-      int x[8];  // ranks 4g .. 4g+7 of this query's row (index 0 when not loaded)
-      if (p.table_u16) {
-        const uint16_t* t16 = static_cast<const uint16_t*>(p.table) + u0.table_off + col;
-        const uint2 v0 = w0 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)g * 4 * n_m))
-                            : make_uint2(0u, 0u);
-        const uint2 v1 = w1 ? __ldg(reinterpret_cast<const uint2*>(t16 + (int64_t)(g + 1) * 4 * n_m))
-                            : make_uint2(0u, 0u);
-        x[0] = v0.x & 0xffffu; x[1] = v0.x >> 16; x[2] = v0.y & 0xffffu; x[3] = v0.y >> 16;
-        x[4] = v1.x & 0xffffu; x[5] = v1.x >> 16; x[6] = v1.y & 0xffffu; x[7] = v1.y >> 16;
-      } else {
-        const int32_t* t32 = static_cast<const int32_t*>(p.table) + u0.table_off + col;
-        const int4 v0 = w0 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)g * 4 * n_m))
-                           : make_int4(0, 0, 0, 0);
-        const int4 v1 = w1 ? __ldg(reinterpret_cast<const int4*>(t32 + (int64_t)(g + 1) * 4 * n_m))
-                           : make_int4(0, 0, 0, 0);
-        x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-        x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-      }
-      // member flags: the map byte's bit b moved to bit c of byte b (the
-      // multiply spreads bits 0..3 to bits 0, 8, 16, 24)
-      uint32_t flags = 0u;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const uint32_t mb = bytes ? (uint32_t)map[x[c]] : ((mw[x[c] >> 5] >> (x[c] & 31)) & 1u);
-        flags |= ((mb * 0x00204081u) & 0x01010101u) << c;
-      }
-      flags &= act & ((w0 ? 0x0f0f0f0fu : 0u) | (w1 ? 0xf0f0f0f0u : 0u));
-      if (W > 0) {
-        // points inside the exclusion window |x - m| <= W are no neighbours
-        // (the row never holds m itself, so W = 0 excludes nothing)
-        uint32_t win = 0u;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          win |= (((unsigned)x[c] - (unsigned)m + (unsigned)W <= 2u * (unsigned)W) ? 1u : 0u) << c;
-        flags &= ~(win * 0x01010101u);
-      }
-      if (flags != 0u) {
-        // one record per realization with members in this step
-#pragma unroll
-        for (int b = 0; b < kTableGroup; ++b) {
-          const uint32_t fb = (flags >> (8 * b)) & 0xffu;
-          if (fb != 0u) {
-            const uint32_t i = (nrec >> (8 * b)) & 0xffu;  // < K: the realization was short
-            s_rec[(b * K + (int)i) * kThreads + tid] = (uint16_t)(((uint32_t)(g >> 1) << 8) | fb);
-            nrec += 1u << (8 * b);
-          }
-        }
-        // per-byte population counts, then the realizations now complete
-        uint32_t v = flags - ((flags >> 1) & 0x55555555u);
-        v = (v & 0x33333333u) + ((v >> 2) & 0x33333333u);
-        counts += (v + (v >> 4)) & 0x0f0f0f0fu;  // each byte stays below K + 8
-        const uint32_t done = ((counts + table_limit) & 0x80808080u) >> 7;  // counts_b >= K
-        act &= ~(done * 0xffu);
-      }
-    }
+    if (bytes)
+      table_walk<K, true, kStats>(p, u0.table_off + col, n_m, groups, m, W, map, s_rec + tid, act,
+                                  counts, nrec, st_entries);
+    else
+      table_walk<K, false, kStats>(p, u0.table_off + col, n_m, groups, m, W, map, s_rec + tid, act,
+                                   counts, nrec, st_entries);
     if (kStats) {
       const uint32_t ent = __reduce_add_sync(kFull, st_entries);
       const unsigned vq = __popc(__ballot_sync(kFull, valid));

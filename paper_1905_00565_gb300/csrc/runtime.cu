@@ -194,7 +194,7 @@ struct TableTuning {
   double crossover, floor, safety;
 };
 TableTuning read_table_tuning() {
-  TableTuning r{40.0, 256.0, 2.0};
+  TableTuning r{20.0, 256.0, 2.0};
   if (const char* e = getenv("CCM_TABLE_CROSSOVER")) r.crossover = std::max(0.0, atof(e));
   if (const char* e = getenv("CCM_TABLE_FLOOR")) r.floor = std::max(16.0, atof(e));
   if (const char* e = getenv("CCM_TABLE_SAFETY")) r.safety = std::max(0.01, atof(e));
@@ -205,7 +205,7 @@ TableTuning read_table_tuning() {
 // scan visits about (E+1)*N_m/L rows per query; brute force (with chunk
 // pruning) costs about L distance evaluations of E coordinates per query.
 // Measured on GB300 (N_m = 10^4, the table build included) the sweep is
-// fastest with c = 40, a floor of 256 and s = 2: L ~ sqrt(c*N_m/(E+1)) is where
+// fastest with c = 20, a floor of 256 and s = 2: L ~ sqrt(c*N_m/(E+1)) is where
 // a grouped table walk overtakes brute force; the floor keeps R, and with it
 // the build's sorts, short.  The last term keeps R = s(E+2)N_m/L + 64 within
 // kTableMaxR.
