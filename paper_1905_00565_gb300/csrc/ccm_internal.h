@@ -169,6 +169,13 @@ __device__ __forceinline__ float sqrt_hw(float x) {
   asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// Hardware reciprocal (rcp.approx.f32: within about one ulp, subnormal inputs
+// included): 1/d_1 of the weights and 1/sum(u_i) of the prediction.
+__device__ __forceinline__ float rcp_hw(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 // The same from the distance d = sqrt_hw(d2) itself.
 __device__ __forceinline__ float simplex_u_dist(float d, float d1, float inv_d1, float wfloor) {
   const float u = (d1 > 0.f) ? __expf(-__fmul_rn(d, inv_d1)) : ((d == 0.f) ? 1.f : 0.f);

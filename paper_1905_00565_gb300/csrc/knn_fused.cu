@@ -414,7 +414,7 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   // and table kernels, the plain comparator and every batch produce the same
   // bits.
   const float d1 = kDist ? dd[0] : sqrt_hw(dd[0]);
-  const float inv_d1 = (d1 > 0.f) ? __frcp_rn(d1) : 0.f;
+  const float inv_d1 = (d1 > 0.f) ? rcp_hw(d1) : 0.f;
   float w[E + 1];
   int nbc[E + 1];
   float usum = 0.f;
@@ -422,9 +422,9 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   for (int s = 0; s <= E; ++s) {
     w[s] = kDist ? simplex_u_dist(dd[s], d1, inv_d1, u.wfloor) : simplex_u(dd[s], d1, inv_d1, u.wfloor);
     usum = __fadd_rn(usum, w[s]);
-    // an unfilled slot (only possible with non-finite device input) reads, and
-    // is reported, in bounds
-    nbc[s] = min(max(nb[s], 0), n_m - 1);
+    // brute force: an unfilled slot (only possible with non-finite device
+    // input) reads, and is reported, in bounds; table entries are in bounds
+    nbc[s] = kDist ? nb[s] : min(max(nb[s], 0), n_m - 1);
     if (kKeep) keep[s * kThreads + tid] = ((u64)__float_as_uint(w[s]) << 32) | (uint32_t)nbc[s];
   }
   auto weight = [&](int s) {
@@ -437,7 +437,7 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
     float acc = 0.f;
 #pragma unroll
     for (int s = 0; s <= E; ++s) acc = __fmaf_rn(weight(s), si[nbr(s) + off], acc);
-    const float xhat = __fdiv_rn(acc, usum);
+    const float xhat = __fmul_rn(acc, rcp_hw(usum));  // usum >= exp(-1)
     if (valid) {
       if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
       if (p.dbg_nbr) {
@@ -1101,7 +1101,7 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
         }
 #pragma unroll
         for (int s2 = 0; s2 <= E; ++s2) {
-          nb[s2] = kl[s2];
+          nb[s2] = min(max(kl[s2], 0), n_m - 1);  // in bounds however few points qualified
           dd[s2] = sqrt_hw(kd[s2]);
         }
       }

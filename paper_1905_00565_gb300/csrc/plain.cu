@@ -58,15 +58,15 @@ plain_knn_kernel(const float* series, const UnitDesc* unit, const TargetDesc* ta
   }
   // simplex projection over the E+1 nearest (the query was never a candidate)
   const float d1 = sqrt_hw(kd[0]);
-  const float inv_d1 = (d1 > 0.f) ? __frcp_rn(d1) : 0.f;
+  const float inv_d1 = (d1 > 0.f) ? rcp_hw(d1) : 0.f;
   float usum = 0.f, accx = 0.f;
   for (int s = 0; s <= E; ++s) {
     const float ui = simplex_u(kd[s], d1, inv_d1, u.wfloor);
     usum = __fadd_rn(usum, ui);
     const int nbc = min(max(kl[s], 0), u.n_m - 1);  // in bounds even for non-finite input
-    accx = fmaf(ui, si[nbc + off], accx);
+    accx = __fmaf_rn(ui, si[nbc + off], accx);
   }
-  xhat[m] = accx / usum;
+  xhat[m] = __fmul_rn(accx, rcp_hw(usum));
 }
 
 __global__ void __launch_bounds__(kRhoThreads)
