@@ -459,10 +459,23 @@ def run_ours(args, rank, world, local_rank, cpu=None):
                           "convergence": sum(conv_ms) / max(1, len(conv_ms))},
             "neighbour_search": {
                 "tables": "distance indexing tables (paper Sect. 3.2), built every step, for "
-                          "L >= sqrt(190 N_m/(E+1)); brute force with exact chunk pruning below",
+                          "L >= max(256, sqrt(20 N_m/(E+1))), rows of R = 2(E+2)N_m/L_min + 64 "
+                          "entries; brute force with exact chunk pruning below",
                 "table_bytes": info["table_bytes"],
                 "brute_force_share_of_pairs": info["brute_pair_count"] / info["pair_count"],
-                "brute_force_share_of_flops": info["brute_flop_count"] / info["flop_count"]},
+                "brute_force_share_of_flops": info["brute_flop_count"] / info["flop_count"],
+                "table_query_share": info["table_query_count"] / max(1, info["search_query_count"])},
+            # the table-scan kernel: the largest stage, but a lookup walk with no
+            # flop or byte count of the exhaustive method to put against a peak
+            "table_scan": {
+                "kernel": "knn_table_kernel<E>, one launch per E per step: each query walks "
+                          "its table row until every realization of its group (up to 4 of a "
+                          "cell) has E+1 library members, then the simplex/moment epilogue",
+                "share_of_step": st[3] / t_step,
+                "query_realizations_per_s": info["table_query_count"] / (st[3] / 1e3),
+                "brute_force_query_realizations_per_s":
+                    (info["search_query_count"] - info["table_query_count"]) / (st[2] / 1e3),
+                "bound": "issue and L2 latency (see the committed ncu summary)"},
             "convergence": {"rows": n_rows, "converged_rows": int(conv_host["converged"].sum()),
                             "test": f"one-sided Jonckheere-Terpstra over the {len(p.L)} L "
                                     "groups, z > 1.645"},

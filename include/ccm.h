@@ -134,6 +134,10 @@ typedef struct {
   size_t table_bytes;         /* distance indexing tables of the plan (0: none) */
   int64_t launches_per_run;   /* kernel launches of one ccm_run (graph nodes) */
   double brute_pair_count;    /* the part of pair_count searched by brute force */
+  int64_t search_query_count; /* neighbour searches: N_m summed over library realizations
+                                 (a library realization serves all targets of its variable) */
+  int64_t table_query_count;  /* the part of search_query_count answered from a distance
+                                 indexing table; the rest are searched by brute force */
 } ccm_plan_info;
 
 typedef struct ccm_context ccm_context;

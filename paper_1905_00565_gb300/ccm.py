@@ -70,7 +70,8 @@ class ccm_plan_info(ctypes.Structure):
                 ("n_work_items", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("pair_count", ctypes.c_double), ("flop_count", ctypes.c_double),
                 ("brute_flop_count", ctypes.c_double), ("table_bytes", ctypes.c_size_t),
-                ("launches_per_run", ctypes.c_int64), ("brute_pair_count", ctypes.c_double)]
+                ("launches_per_run", ctypes.c_int64), ("brute_pair_count", ctypes.c_double),
+                ("search_query_count", ctypes.c_int64), ("table_query_count", ctypes.c_int64)]
 
 
 class ccm_search_stats(ctypes.Structure):

@@ -158,28 +158,34 @@ enum : int {
 constexpr int kDefaultMergeAt = 4;
 constexpr int kDefaultVariant = 1;
 
-// Simplex weight (paper Sect. 2.1) of a neighbour at squared distance d2 when
-// the nearest is at distance d1 (> 0; inv_d1 = 1/d1): u = exp(-d/d1), raised
-// to the floor f.  d1 = 0 takes the limit: 1 for d = 0, else 0.  Shared by the
-// fused kernels and the plain comparator so that all compute the same bits;
-// FP32 with the hardware square root and exponential (relative error near
-// 1e-7, far inside the 1e-5 the predictions are checked to).
+// Hardware square root and reciprocal (sqrt.approx.f32, rcp.approx.f32:
+// within about one ulp, subnormal inputs included).
 __device__ __forceinline__ float sqrt_hw(float x) {
   float r;
   asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// Hardware reciprocal (rcp.approx.f32: within about one ulp, subnormal inputs
-// included): 1/d_1 of the weights and 1/sum(u_i) of the prediction.
 __device__ __forceinline__ float rcp_hw(float x) {
   float r;
   asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// The same from the distance d = sqrt_hw(d2) itself.
+
+// Simplex weight (paper Sect. 2.1) of a neighbour at distance d = sqrt_hw(d2)
+// when the nearest is at distance d1 (> 0; inv_d1 = rcp_hw(d1)): u =
+// exp(-d/d1), raised to the floor f.  d1 = 0 takes the limit: 1 for d = 0,
+// else 0.  Shared by the fused kernels and the plain comparator so that all
+// compute the same bits; FP32 with the hardware square root, reciprocal and
+// exponential (relative error near 1e-7, far inside the 1e-5 the predictions
+// are checked to).  The two cases separately, then together:
+__device__ __forceinline__ float simplex_exp(float d, float inv_d1) {  // d1 > 0
+  return __expf(-__fmul_rn(d, inv_d1));
+}
+__device__ __forceinline__ float simplex_limit(float d) {  // d1 = 0
+  return (d == 0.f) ? 1.f : 0.f;
+}
 __device__ __forceinline__ float simplex_u_dist(float d, float d1, float inv_d1, float wfloor) {
-  const float u = (d1 > 0.f) ? __expf(-__fmul_rn(d, inv_d1)) : ((d == 0.f) ? 1.f : 0.f);
-  return fmaxf(u, wfloor);
+  return fmaxf((d1 > 0.f) ? simplex_exp(d, inv_d1) : simplex_limit(d), wfloor);
 }
 __device__ __forceinline__ float simplex_u(float d2, float d1, float inv_d1, float wfloor) {
   return simplex_u_dist(sqrt_hw(d2), d1, inv_d1, wfloor);

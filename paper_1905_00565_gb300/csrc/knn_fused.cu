@@ -418,9 +418,17 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
   float w[E + 1];
   int nbc[E + 1];
   float usum = 0.f;
+  // simplex_u_dist with the d1 > 0 test taken once: the exponential for every
+  // neighbour, replaced by the limit in the rare query whose nearest is at 0
+#pragma unroll
+  for (int s = 0; s <= E; ++s) w[s] = simplex_exp(kDist ? dd[s] : sqrt_hw(dd[s]), inv_d1);
+  if (!(d1 > 0.f)) {
+#pragma unroll
+    for (int s = 0; s <= E; ++s) w[s] = simplex_limit(kDist ? dd[s] : sqrt_hw(dd[s]));
+  }
 #pragma unroll
   for (int s = 0; s <= E; ++s) {
-    w[s] = kDist ? simplex_u_dist(dd[s], d1, inv_d1, u.wfloor) : simplex_u(dd[s], d1, inv_d1, u.wfloor);
+    w[s] = fmaxf(w[s], u.wfloor);
     usum = __fadd_rn(usum, w[s]);
     // brute force: an unfilled slot (only possible with non-finite device
     // input) reads, and is reported, in bounds; table entries are in bounds

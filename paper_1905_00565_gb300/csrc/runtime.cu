@@ -178,6 +178,8 @@ struct UnitList {
   }
   double brute_flops = 0.0;           // 3E per pair of the units searched by brute force
   double brute_pairs = 0.0;           // query-library pairs of those units
+  int64_t search_queries = 0;         // N_m summed over the units
+  int64_t table_queries = 0;          // N_m summed over the units that read a table
   int table_u16() const { return max_nm < 65536 ? 1 : 0; }
   size_t table_elem() const { return table_u16() ? 2 : 4; }
   int64_t n_rho = 0, q_total = 0, nbr_total = 0, lib_dbg_total = 0;  // per output realization
@@ -433,7 +435,10 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
             if (u.table_R == 0) {
               ul->brute_flops += 3.0 * E * (double)u.n_m * (double)L;
               ul->brute_pairs += (double)u.n_m * (double)L;
+            } else {
+              ul->table_queries += u.n_m;
             }
+            ul->search_queries += u.n_m;
             ul->lib_total += L;
             ul->part_total += (int64_t)u.n_tiles * u.n_targets;
             ul->emin = std::min(ul->emin, E);
@@ -1071,6 +1076,8 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.flop_count = pl->ul.flops;
   in.brute_flop_count = pl->ul.brute_flops;
   in.brute_pair_count = pl->ul.brute_pairs;
+  in.search_query_count = pl->ul.search_queries;
+  in.table_query_count = pl->ul.table_queries;
   in.table_bytes = (pl->ul.table_elem() + sizeof(float)) * (size_t)pl->ul.table_total;
   // launches of one ccm_run: order, tables, sampler, one brute-force and one
   // table-scan kernel per E present
