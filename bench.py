@@ -459,8 +459,9 @@ def run_ours(args, rank, world, local_rank, cpu=None):
                           "convergence": sum(conv_ms) / max(1, len(conv_ms))},
             "neighbour_search": {
                 "tables": "distance indexing tables (paper Sect. 3.2), built every step, for "
-                          "L >= max(256, sqrt(20 N_m/(E+1))), rows of R = 2(E+2)N_m/L_min + 64 "
-                          "entries; brute force with exact chunk pruning below",
+                          "L >= max(256, sqrt(20 N_m/(E+1)), N_m/40), rows of R entries so that a "
+                          "query at the smallest such L misses its E+1 members with probability "
+                          "<= 1/(10 L); brute force with exact chunk pruning below",
                 "table_bytes": info["table_bytes"],
                 "brute_force_share_of_pairs": info["brute_pair_count"] / info["pair_count"],
                 "brute_force_share_of_flops": info["brute_flop_count"] / info["flop_count"],

@@ -75,10 +75,11 @@ typedef enum {
                                       where that is faster and the tables fit a quarter of
                                       the context budget; results are identical either way.
                                       Tuning knobs (environment, read at each ccm_plan):
-                                      CCM_TABLE_SAFETY (default 2: table row length over the
-                                      expected scan length), CCM_TABLE_CROSSOVER (default
-                                      20) and CCM_TABLE_FLOOR (default 256): tables for
-                                      L >= max(floor, sqrt(c*N_m/(E+1))) */
+                                      CCM_TABLE_CROSSOVER (default 20), CCM_TABLE_FLOOR
+                                      (default 256) and CCM_TABLE_MAX_RATIO (default 40):
+                                      tables for L >= max(floor, sqrt(c*N_m/(E+1)),
+                                      N_m/max_ratio); CCM_TABLE_SAFETY (default 1): factor
+                                      on the table row length */
 #define CCM_SEARCH_STATS     0x20u /* the neighbour-search kernels also count their work
                                       (ccm_plan_search_stats); a separately compiled
                                       counting variant, slower, same results */

@@ -187,33 +187,60 @@ struct UnitList {
   double pairs = 0.0, flops = 0.0;    // neighbour-search work actually done
 };
 
-// Table tunables: the crossover constant c and the floor of table_min_L, and
-// the safety factor s of R over the expected scan length (see below).  The
-// environment variables CCM_TABLE_CROSSOVER, CCM_TABLE_FLOOR and
-// CCM_TABLE_SAFETY replace the defaults (read at each ccm_plan; tuning and
-// measurement only).
+// Table tunables: the crossover constant c, the floor and the largest
+// manifold-to-library ratio of table_min_L, and a factor s on the row length
+// (see below).  The environment variables CCM_TABLE_CROSSOVER, CCM_TABLE_FLOOR,
+// CCM_TABLE_MAX_RATIO and CCM_TABLE_SAFETY replace the defaults (read at each
+// ccm_plan; tuning and measurement only).
 struct TableTuning {
-  double crossover, floor, safety;
+  double crossover, floor, max_ratio, safety;
 };
 TableTuning read_table_tuning() {
-  TableTuning r{20.0, 256.0, 2.0};
+  TableTuning r{20.0, 256.0, 40.0, 1.0};
   if (const char* e = getenv("CCM_TABLE_CROSSOVER")) r.crossover = std::max(0.0, atof(e));
   if (const char* e = getenv("CCM_TABLE_FLOOR")) r.floor = std::max(16.0, atof(e));
+  if (const char* e = getenv("CCM_TABLE_MAX_RATIO")) r.max_ratio = std::max(1.0, atof(e));
   if (const char* e = getenv("CCM_TABLE_SAFETY")) r.safety = std::max(0.01, atof(e));
   return r;
 }
 
 // Smallest L whose realizations read a distance indexing table.  A table
-// scan visits about (E+1)*N_m/L rows per query; brute force (with chunk
-// pruning) costs about L distance evaluations of E coordinates per query.
-// Measured on GB300 (N_m = 10^4, the table build included) the sweep is
-// fastest with c = 20, a floor of 256 and s = 2: L ~ sqrt(c*N_m/(E+1)) is where
-// a grouped table walk overtakes brute force; the floor keeps R, and with it
-// the build's sorts, short.  The last term keeps R = s(E+2)N_m/L + 64 within
+// walk visits about (E+1)*N_m/L row entries per query; brute force (with chunk
+// pruning) costs about L distance evaluations of E coordinates per query, far
+// fewer at small E, where pruning skips most chunks.  Measured on GB300: on
+// the N_m = 10^4 sweep (the table build included) c = 20 and a floor of 256
+// are fastest, L ~ sqrt(c*N_m/(E+1)) being where a grouped table walk
+// overtakes the selection-bound brute force of small libraries; on the
+// N = 10^5 series (E = 3..6) brute force at L = 1000 beats walks of
+// (E+1)*100 entries, so libraries below N_m/max_ratio (40) points stay with
+// brute force.  The last term keeps the row length (table_row_length) within
 // kTableMaxR.
 double table_min_L(int32_t E, int64_t n_m, const TableTuning& t) {
   return std::max({t.floor, std::ceil(std::sqrt(t.crossover * (double)n_m / (double)(E + 1))),
-                   std::ceil(t.safety * (E + 2) * (double)n_m / (double)(kTableMaxR - 64))});
+                   std::ceil((double)n_m / t.max_ratio),
+                   std::ceil(t.safety * 2.8 * (E + 2) * (double)n_m / (double)kTableMaxR)});
+}
+
+// Row length R of a table whose smallest L is lmin.  A query of a realization
+// with L = lmin finds a Poisson(lambda = R*lmin/N_m) number of its library's
+// points among its R entries (the library is a uniform sample); with fewer
+// than E+1 it scans its whole library instead, about lmin distance
+// evaluations.  lambda is the smallest multiple of 1/4 for which that happens
+// with probability at most 1/(10*lmin), so the misses cost at most about 0.1
+// distance evaluations a query (times the safety factor s on lambda); 2W more
+// entries cover the points the exclusion window removes.
+int64_t table_row_length(int32_t E, int64_t n_m, int64_t lmin, int32_t theiler, double safety) {
+  const double eps = 1.0 / (10.0 * (double)lmin);
+  double lambda = (double)(E + 1);
+  for (;; lambda += 0.25) {
+    double term = std::exp(-lambda), tail = term;  // P(X <= E), X ~ Poisson(lambda)
+    for (int i = 1; i <= E; ++i) {
+      term *= lambda / i;
+      tail += term;
+    }
+    if (tail <= eps) break;
+  }
+  return (int64_t)std::ceil(safety * lambda * (double)n_m / (double)lmin) + 2 * (int64_t)theiler;
 }
 
 // Append the units of one problem.  Offsets: series block, first rho index.
@@ -300,15 +327,15 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
         }
   // Distance indexing tables (unless CCM_NO_TABLE): per (j, E, tau),
   // realizations with L >= table_min_L read their neighbours from a table of
-  // the R nearest points of every query; R covers s times the expected
-  // scan length (E+2)*N_m/L at the smallest such L.  A table is built only when the
+  // the R nearest points of every query (R from table_row_length at the
+  // smallest such L).  A table is built only when the
   // realizations that use it would otherwise scan at least 8*N_m library
   // points in total (its build costs about N_m^2 distance evaluations), and
   // while the plan's tables stay within table_cap_bytes; the realizations of
   // a (j, E, tau) without a table use brute force.
   std::map<std::tuple<int32_t, int32_t, int32_t>, std::pair<int64_t, int32_t>> table_of;
-  // Safety factor of R over the expected scan length: table memory and build
-  // time against how often a query falls back to scanning its library.
+  // The safety factor trades table memory and build time against how often a
+  // query falls back to scanning its library.
   const TableTuning tt = read_table_tuning();
   const double safety = tt.safety;
   double table_bytes = 0.0;
@@ -327,9 +354,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
               lsum += (double)L * pc.r;
             }
           if (lmin < 0 || lsum < 8.0 * (double)n_m) continue;
-          // the window removes up to 2W more of the nearest points from every row
-          int64_t R = (int64_t)std::ceil(safety * (E + 2) * (double)n_m / (double)lmin) + 64 +
-                      2 * (int64_t)pc.theiler;
+          int64_t R = table_row_length(E, n_m, lmin, pc.theiler, safety);
           // whole groups of four ranks (the table's layout), from the n_m - 1
           // points other than the query
           R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR),
