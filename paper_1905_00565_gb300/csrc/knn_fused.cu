@@ -528,6 +528,13 @@ __device__ __noinline__ void stage_library(const float* sj, const int32_t* lib, 
   }
 }
 
+// The library position (in query order) about as far into the library as
+// query position pos is into the manifold: floor(L*pos/N_m), in FP32 (only a
+// starting point of the scan: any value in [0, L) gives the same result).
+__device__ __forceinline__ int library_position(int L, int pos, int n_m) {
+  return min(L - 1, __float2int_rz(__fmul_rn((float)L, __fdividef((float)pos, (float)n_m))));
+}
+
 // The running threshold: t[0..K) holds the K smallest squared distances (as
 // values, ties repeated) of the candidates seen so far, ascending.  Inserting
 // x is a min/max network: slot s becomes min(t[s], max(t[s-1], x)), which
@@ -657,7 +664,7 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
       qhi[e] = hi;
     }
     // the library position nearest this warp's queries (in query order)
-    const int aw = (int)((int64_t)L * (int64_t)(tile * kQT + warp * 32) / n_m);
+    const int aw = library_position(L, tile * kQT + warp * 32, n_m);
 
     float tl[K];  // running threshold: the K smallest distances so far, ascending
 #pragma unroll
@@ -823,7 +830,7 @@ __device__ void process_item(const KnnParams& p, const UnitDesc& u, int unit, in
     // nearest this query tile (the same order in every warp: the staging is
     // block-wide).
     const int ntiles = single ? 1 : (L + LT - 1) / LT;
-    const int first_t = single ? 0 : (int)((int64_t)L * (int64_t)(tile * kQT) / n_m) / LT;
+    const int first_t = single ? 0 : library_position(L, tile * kQT, n_m) / LT;
     for (int c = 0; c < ntiles; ++c) {
       int ti = first_t + c;
       ti -= (ti >= ntiles) ? ntiles : 0;
