@@ -31,7 +31,7 @@ struct UnitDesc {
   int32_t table_R;      // > 0: neighbours read from the table (R entries per query)
   int32_t theiler;      // exclusion window W >= 0: candidates l of query m need |l - m| > W
   float wfloor;         // simplex weight floor f >= 0: u_i = max(u_i, f)
-  int32_t pad;
+  int32_t table_tv;     // 1: the table also holds this unit's (single) target's values
 };
 
 // One target of a unit: the pair (j, i) and where its outputs go.
@@ -96,7 +96,7 @@ struct TableJob {
   int64_t order_off;    // query order of this combination
   int64_t table_off;    // first entry: table[table_off + r * n_m + pos]
   int32_t j, E, tau, n_m, R;
-  int32_t pad;
+  int32_t tv_i;         // >= 0: also store target variable tv_i's value at every entry's point
 };
 constexpr int kTableMaxR = 2048;       // entries per query row, at most
 constexpr int kTableChunk = 8;         // query tiles per table work item (one bitmap each)
@@ -123,6 +123,7 @@ struct KnnParams {
   const int32_t* order;   // query order (manifold index per position)
   const void* table;      // distance indexing tables (units with table_R > 0)
   const float* table_dist;  // every table entry's distance sqrt_hw(FP32 squared distance), same layout
+  const float* table_tv;  // for tables with a target (TableJob::tv_i): its value at each entry's point
   int32_t table_u16;      // 1: uint16 entries (every manifold below 65536 points), 0: int32
   double* partials;       // 6 doubles per query tile
   const double* obs;      // observed-moment tile records (TargetDesc::obs_tile)
@@ -212,7 +213,7 @@ cudaError_t table_prepare();
 // One launch builds the tables of jobs[0..n_jobs), all of embedding dimension E.
 cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs, int E,
                                int max_nm, int max_R, const int32_t* order, void* table,
-                               float* table_dist, int table_u16, cudaStream_t s);
+                               float* table_dist, float* table_tv, int table_u16, cudaStream_t s);
 
 // Fused kernel (knn_fused.cu).
 int knn_block_threads();

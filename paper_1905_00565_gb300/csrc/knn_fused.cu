@@ -397,13 +397,15 @@ __device__ __forceinline__ void flush_ring(const KnnParams& p, const float* ring
 // holds the weights and neighbours in shared memory, so that a reduction
 // between two targets finds no live registers to spill; other warps may still
 // be searching, so nothing else of the buffer is touched.  kKeep false: they
-// stay in registers.
+// stay in registers.  nb_values (table path, one target, no checking copy of
+// the neighbours): nb holds the bits of the target's values at the E+1
+// neighbours, read from the table instead of gathered.
 static_assert(kMaxE + 1 <= kBuf, "the epilogue keeps E+1 entries in a candidate column");
 template <int E, bool kKeep, bool kDist = false>
 __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& u, int unit,
                                             int tile, int m, bool valid, const float (&dd)[E + 1],
                                             const int (&nb)[E + 1], float* ring, RingMeta* meta,
-                                            int& ring_n, u64* keep) {
+                                            int& ring_n, u64* keep, bool nb_values = false) {
   const int tid = threadIdx.x;
   const int n_m = u.n_m;
   const int off = (E - 1) * u.tau;
@@ -443,8 +445,13 @@ __device__ __forceinline__ void finish_tile(const KnnParams& p, const UnitDesc& 
     const TargetDesc tg = p.targets[u.tgt_off + t];
     const float* si = p.series + u.series_off + (int64_t)tg.i * u.n;
     float acc = 0.f;
+    if (nb_values) {  // nb holds the table's copy of the target at the neighbours
 #pragma unroll
-    for (int s = 0; s <= E; ++s) acc = __fmaf_rn(weight(s), si[nbr(s) + off], acc);
+      for (int s = 0; s <= E; ++s) acc = __fmaf_rn(weight(s), __int_as_float(nbr(s)), acc);
+    } else {
+#pragma unroll
+      for (int s = 0; s <= E; ++s) acc = __fmaf_rn(weight(s), si[nbr(s) + off], acc);
+    }
     const float xhat = __fmul_rn(acc, rcp_hw(usum));  // usum >= exp(-1)
     if (valid) {
       if (p.dbg_xhat) p.dbg_xhat[tg.q_off + m] = xhat;
@@ -1063,6 +1070,8 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
       }
       int nb[E + 1];
       float dd[E + 1];
+      // target values from the table (not when the neighbours are checked)
+      bool tv = u.table_tv != 0 && p.table_tv != nullptr && p.dbg_nbr == nullptr;
       if (full || !valid) {
         // the first E+1 flagged ranks of the realization's records; their
         // indices and distances are read from the table (the stored distances
@@ -1080,7 +1089,10 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
           cur &= ~(1u << c);
           const int rank = 8 * (int)(cur >> 8) + c;
           const int64_t at = u0.table_off + (int64_t)(rank >> 2) * 4 * n_m + col + (rank & 3);
+          // the target's value at the neighbour when the table holds it, else
+          // the neighbour's index (for the gather)
           nb[s2] = !valid ? 0
+                   : tv   ? __float_as_int(__ldg(p.table_tv + at))
                           : (p.table_u16 ? (int)__ldg(static_cast<const uint16_t*>(p.table) + at)
                                          : __ldg(static_cast<const int32_t*>(p.table) + at));
           dd[s2] = valid ? __ldg(p.table_dist + at) : 0.f;  // a distance, not squared
@@ -1119,8 +1131,10 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
           nb[s2] = min(max(kl[s2], 0), n_m - 1);  // in bounds however few points qualified
           dd[s2] = sqrt_hw(kd[s2]);
         }
+        tv = false;  // gathered as for brute force
       }
-      finish_tile<E, false, true>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr);
+      finish_tile<E, false, true>(p, u, unit, tile, m, valid, dd, nb, s_ring, meta, ring_n, nullptr,
+                                  tv);
     }
   }
 }

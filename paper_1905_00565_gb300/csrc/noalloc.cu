@@ -116,7 +116,7 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout lay, 
     u.table_R = 0;
     u.theiler = 0;
     u.wfloor = 0.f;
-    u.pad = 0;
+    u.table_tv = 0;
     TargetDesc tg;
     tg.out_idx = k;
     tg.q_off = k * (int64_t)c.n_m;

@@ -180,6 +180,7 @@ struct UnitList {
   double brute_pairs = 0.0;           // query-library pairs of those units
   int64_t search_queries = 0;         // N_m summed over the units
   int64_t table_queries = 0;          // N_m summed over the units that read a table
+  bool table_tv = false;              // some table stores its target's values (TableJob::tv_i)
   int table_u16() const { return max_nm < 65536 ? 1 : 0; }
   size_t table_elem() const { return table_u16() ? 2 : 4; }
   int64_t n_rho = 0, q_total = 0, nbr_total = 0, lib_dbg_total = 0;  // per output realization
@@ -359,8 +360,14 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
           // points other than the query
           R = std::min<int64_t>(std::min<int64_t>((R + 31) / 32 * 32, kTableMaxR),
                                 (n_m - 1) / 4 * 4);
-          // indices (2 or 4 bytes) and FP32 squared distances
-          const double bytes = (double)n_m * (double)R * ((n_m < 65536 ? 2.0 : 4.0) + 4.0);
+          // indices (2 or 4 bytes), distances, and (a variable with one target,
+          // a manifold below 65536 points) the target's values: the scan then
+          // reads them beside the distances instead of gathering them through
+          // the indices (on longer manifolds the extra array's cold lines cost
+          // more than the gather: 120 -> 129 ms on the N = 10^5 series)
+          const bool tv = pairs_of[j].size() == 1 && n_m < 65536;
+          const double bytes =
+              (double)n_m * (double)R * ((n_m < 65536 ? 2.0 : 4.0) + 4.0 + (tv ? 4.0 : 0.0));
           if (table_bytes + bytes > table_cap_bytes) continue;
           table_bytes += bytes;
           TableJob tj;
@@ -374,6 +381,8 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
           tj.tau = tau;
           tj.n_m = (int32_t)n_m;
           tj.R = (int32_t)R;
+          tj.tv_i = tv ? pc.pairs[2 * pairs_of[j][0] + 1] : -1;
+          if (tv) ul->table_tv = true;
           table_of[std::make_tuple(j, E, tau)] = std::make_pair(tj.table_off, tj.R);
           ul->table_total += n_m * R;
           ul->tables.push_back(tj);
@@ -422,6 +431,7 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
             if (tab != table_of.end() && (double)L >= table_min_L(E, u.n_m, tt)) {
               u.table_off = tab->second.first;
               u.table_R = tab->second.second;
+              u.table_tv = (tp.size() == 1 && u.n_m < 65536) ? 1 : 0;  // as the table's job
             }
             const int32_t uidx = (int32_t)ul->units.size();
             // Table realizations of one cell with a single target and a byte
@@ -548,7 +558,8 @@ void sort_items(UnitList* ul) {
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
          counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
-         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_dist = 0, stats = 0,
+         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_dist = 0, table_tv = 0,
+         stats = 0,
          total = 0;
 };
 
@@ -576,6 +587,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.targets = take(sizeof(TargetDesc) * ul.targets.size());
   a.table = take(ul.table_elem() * (size_t)ul.table_total);
   a.table_dist = take(sizeof(float) * (size_t)ul.table_total);
+  a.table_tv = take(ul.table_tv ? sizeof(float) * (size_t)ul.table_total : 0);
   a.tables = take(sizeof(TableJob) * ul.tables.size());
   a.items_table = take(sizeof(WorkItem) * ul.items_table.size());
   a.obs = take(sizeof(double) * kObsStride * (size_t)ul.obs_total);
@@ -742,6 +754,7 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.order = reinterpret_cast<const int32_t*>(base + ar.order);
   kp.table = base + ar.table;
   kp.table_dist = reinterpret_cast<const float*>(base + ar.table_dist);
+  kp.table_tv = ul.table_tv ? reinterpret_cast<const float*>(base + ar.table_tv) : nullptr;
   kp.table_u16 = ul.table_u16();
   kp.partials = reinterpret_cast<double*>(base + ar.part);
   kp.obs = reinterpret_cast<const double*>(base + ar.obs);
@@ -806,6 +819,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                                 (int64_t)(g1 - g0), te, nm, rmax,
                                 reinterpret_cast<const int32_t*>(base + ar.order),
                                 base + ar.table, reinterpret_cast<float*>(base + ar.table_dist),
+                                ul.table_tv ? reinterpret_cast<float*>(base + ar.table_tv) : nullptr,
                                 ul.table_u16(), s));
     g0 = g1;
   }
@@ -1103,7 +1117,8 @@ ccm_status ccm_plan(ccm_context* ctx, const ccm_problem* prob, ccm_plan_t** out)
   in.brute_pair_count = pl->ul.brute_pairs;
   in.search_query_count = pl->ul.search_queries;
   in.table_query_count = pl->ul.table_queries;
-  in.table_bytes = (pl->ul.table_elem() + sizeof(float)) * (size_t)pl->ul.table_total;
+  in.table_bytes = (pl->ul.table_elem() + sizeof(float) * (pl->ul.table_tv ? 2 : 1)) *
+                   (size_t)pl->ul.table_total;
   // launches of one ccm_run: order, tables, sampler, one brute-force and one
   // table-scan kernel per E present
   in.launches_per_run = 3 + pl->ul.table_groups();  // order, observed moments, sampler, tables
