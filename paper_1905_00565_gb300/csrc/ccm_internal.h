@@ -122,8 +122,9 @@ struct KnnParams {
   const int32_t* lib;
   const int32_t* order;   // query order (manifold index per position)
   const void* table;      // distance indexing tables (units with table_R > 0)
-  const float* table_dist;  // every table entry's distance sqrt_hw(FP32 squared distance), same layout
-  const float* table_tv;  // for tables with a target (TableJob::tv_i): its value at each entry's point
+  const float* table_dist;  // every table entry's distance sqrt_hw(FP32 squared distance), same
+                            // layout; table_pairs: float2 {distance, target value} per entry
+  int32_t table_pairs;    // 1: the tables store (distance, target value) pairs (TableJob::tv_i)
   int32_t table_u16;      // 1: uint16 entries (every manifold below 65536 points), 0: int32
   double* partials;       // 6 doubles per query tile
   const double* obs;      // observed-moment tile records (TargetDesc::obs_tile)
@@ -213,7 +214,7 @@ cudaError_t table_prepare();
 // One launch builds the tables of jobs[0..n_jobs), all of embedding dimension E.
 cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs, int E,
                                int max_nm, int max_R, const int32_t* order, void* table,
-                               float* table_dist, float* table_tv, int table_u16, cudaStream_t s);
+                               float* table_dist, int table_pairs, int table_u16, cudaStream_t s);
 
 // Fused kernel (knn_fused.cu).
 int knn_block_threads();

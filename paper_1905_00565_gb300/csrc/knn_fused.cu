@@ -1071,7 +1071,7 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
       int nb[E + 1];
       float dd[E + 1];
       // target values from the table (not when the neighbours are checked)
-      bool tv = u.table_tv != 0 && p.table_tv != nullptr && p.dbg_nbr == nullptr;
+      bool tv = u.table_tv != 0 && p.table_pairs && p.dbg_nbr == nullptr;
       if (full || !valid) {
         // the first E+1 flagged ranks of the realization's records; their
         // indices and distances are read from the table (the stored distances
@@ -1087,15 +1087,31 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
           const uint32_t fl = cur & 0xffu;
           const int c = fl ? __ffs(fl) - 1 : 0;  // fl > 0 whenever the walk was full
           cur &= ~(1u << c);
-          const int rank = 8 * (int)(cur >> 8) + c;
-          const int64_t at = u0.table_off + (int64_t)(rank >> 2) * 4 * n_m + col + (rank & 3);
-          // the target's value at the neighbour when the table holds it, else
-          // the neighbour's index (for the gather)
-          nb[s2] = !valid ? 0
-                   : tv   ? __float_as_int(__ldg(p.table_tv + at))
-                          : (p.table_u16 ? (int)__ldg(static_cast<const uint16_t*>(p.table) + at)
-                                         : __ldg(static_cast<const int32_t*>(p.table) + at));
-          dd[s2] = valid ? __ldg(p.table_dist + at) : 0.f;  // a distance, not squared
+          nb[s2] = 8 * (int)(cur >> 8) + c;  // the rank, for now
+        }
+        // the distances (not squared) and, when the table holds them, the
+        // target's values at the neighbours (one 8-byte load each), else the
+        // neighbours' indices (for the gather)
+        auto at = [&](int rank) {
+          return u0.table_off + (int64_t)(rank >> 2) * 4 * n_m + col + (rank & 3);
+        };
+        const float2* dv2 = reinterpret_cast<const float2*>(p.table_dist);
+        if (tv) {
+#pragma unroll
+          for (int s2 = 0; s2 <= E; ++s2) {
+            const float2 dv = valid ? __ldg(dv2 + at(nb[s2])) : make_float2(0.f, 0.f);
+            dd[s2] = dv.x;
+            nb[s2] = __float_as_int(dv.y);
+          }
+        } else {
+#pragma unroll
+          for (int s2 = 0; s2 <= E; ++s2) {
+            const int64_t a2 = at(nb[s2]);
+            dd[s2] = !valid ? 0.f : p.table_pairs ? __ldg(dv2 + a2).x : __ldg(p.table_dist + a2);
+            nb[s2] = !valid ? 0
+                            : (p.table_u16 ? (int)__ldg(static_cast<const uint16_t*>(p.table) + a2)
+                                           : __ldg(static_cast<const int32_t*>(p.table) + a2));
+          }
         }
       } else {
         // Rare: fewer than E+1 members among the R nearest points; scan the

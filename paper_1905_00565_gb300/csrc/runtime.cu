@@ -558,8 +558,7 @@ void sort_items(UnitList* ul) {
 struct Arena {
   size_t series = 0, units = 0, items = 0, lib = 0, part = 0, done = 0, rho = 0, err = 0,
          counter = 0, scratch = 0, order = 0, orders = 0, targets = 0, table = 0, tables = 0,
-         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_dist = 0, table_tv = 0,
-         stats = 0,
+         items_table = 0, order_scratch = 0, obs = 0, obs_jobs = 0, table_dist = 0, stats = 0,
          total = 0;
 };
 
@@ -586,8 +585,7 @@ Arena layout(int64_t series_elems, const UnitList& ul, int64_t n_rho, int64_t sc
   a.orders = take(sizeof(OrderJob) * ul.orders.size());
   a.targets = take(sizeof(TargetDesc) * ul.targets.size());
   a.table = take(ul.table_elem() * (size_t)ul.table_total);
-  a.table_dist = take(sizeof(float) * (size_t)ul.table_total);
-  a.table_tv = take(ul.table_tv ? sizeof(float) * (size_t)ul.table_total : 0);
+  a.table_dist = take((ul.table_tv ? sizeof(float2) : sizeof(float)) * (size_t)ul.table_total);
   a.tables = take(sizeof(TableJob) * ul.tables.size());
   a.items_table = take(sizeof(WorkItem) * ul.items_table.size());
   a.obs = take(sizeof(double) * kObsStride * (size_t)ul.obs_total);
@@ -754,7 +752,7 @@ KnnParams knn_params(char* base, const Arena& ar, const UnitList& ul, int persis
   kp.order = reinterpret_cast<const int32_t*>(base + ar.order);
   kp.table = base + ar.table;
   kp.table_dist = reinterpret_cast<const float*>(base + ar.table_dist);
-  kp.table_tv = ul.table_tv ? reinterpret_cast<const float*>(base + ar.table_tv) : nullptr;
+  kp.table_pairs = ul.table_tv ? 1 : 0;
   kp.table_u16 = ul.table_u16();
   kp.partials = reinterpret_cast<double*>(base + ar.part);
   kp.obs = reinterpret_cast<const double*>(base + ar.obs);
@@ -819,7 +817,7 @@ ccm_status enqueue_sweep(char* base, const Arena& ar, const UnitList& ul, const 
                                 (int64_t)(g1 - g0), te, nm, rmax,
                                 reinterpret_cast<const int32_t*>(base + ar.order),
                                 base + ar.table, reinterpret_cast<float*>(base + ar.table_dist),
-                                ul.table_tv ? reinterpret_cast<float*>(base + ar.table_tv) : nullptr,
+                                ul.table_tv ? 1 : 0,
                                 ul.table_u16(), s));
     g0 = g1;
   }

@@ -146,7 +146,7 @@ __device__ __forceinline__ uint32_t d2_bits_staged(const float* stage, int off, 
 // series values, or null.
 template <int E>
 __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
-                          const int32_t* order, void* table, float* table_dist, float* table_tv,
+                          const int32_t* order, void* table, float* table_dist, int pairs,
                           const float* tv_series, int u16,
                           uint32_t* hist, unsigned long long* keys, unsigned long long* bnd,
                           uint32_t* cnt, int region_keys, float* stage) {
@@ -372,13 +372,17 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
   }
   __syncwarp();
   const int64_t base = jb.table_off + (int64_t)pos * 4;
-  for (int r = lane; r < R; r += 32)  // each entry's distance (the epilogue's square root), beside it
-    table_dist[base + (int64_t)(r >> 2) * 4 * n_m + (r & 3)] =
-        sqrt_hw(__uint_as_float((uint32_t)(keys[r] >> 32)));
-  if (jb.tv_i >= 0) {  // the target's value at each entry's point: what the prediction weighs
-    for (int r = lane; r < R; r += 32)
-      table_tv[base + (int64_t)(r >> 2) * 4 * n_m + (r & 3)] =
-          tv_series[(int)(keys[r] & 0xffffffffu) + off];
+  // each entry's distance (the epilogue's square root), beside it; with pairs,
+  // together with the target's value at the entry's point (what the
+  // prediction weighs; 0 in a table without a target)
+  for (int r = lane; r < R; r += 32) {
+    const int64_t at = base + (int64_t)(r >> 2) * 4 * n_m + (r & 3);
+    const float d = sqrt_hw(__uint_as_float((uint32_t)(keys[r] >> 32)));
+    if (pairs)
+      reinterpret_cast<float2*>(table_dist)[at] =
+          make_float2(d, jb.tv_i >= 0 ? tv_series[(int)(keys[r] & 0xffffffffu) + off] : 0.f);
+    else
+      table_dist[at] = d;
   }
   if (u16) {
     uint16_t* out = static_cast<uint16_t*>(table) + base;
@@ -395,7 +399,7 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
 template <int E>
 __global__ void __launch_bounds__(kTableWarps * 32, 2)
 table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
-                   float* table_dist, float* table_tv, int u16, int rcap, int staged) {
+                   float* table_dist, int pairs, int u16, int rcap, int staged) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_cnt[kTableWarps][2];  // per warp: entries below b1, entries of b1
   const TableJob jb = jobs[blockIdx.y];
@@ -416,7 +420,7 @@ table_build_kernel(const float* series, const TableJob* jobs, const int32_t* ord
                      ? reinterpret_cast<float*>(smem + kTableWarps * table_warp_bytes(rcap))
                      : nullptr;
   const float* tv_series = series + jb.series_off + (int64_t)(jb.tv_i >= 0 ? jb.tv_i : 0) * jb.n;
-  build_row<E>(s, jb, pos, pos < jb.n_m, order, table, table_dist, table_tv, tv_series, u16, hist,
+  build_row<E>(s, jb, pos, pos < jb.n_m, order, table, table_dist, pairs, tv_series, u16, hist,
                keys, bnd,
                s_cnt[warp], (int)(table_warp_bytes(rcap) / 8), stage);
 }
@@ -445,7 +449,7 @@ cudaError_t table_prepare() {
 
 cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_t n_jobs, int E,
                                int max_nm, int max_R, const int32_t* order, void* table,
-                               float* table_dist, float* table_tv, int table_u16, cudaStream_t s) {
+                               float* table_dist, int table_pairs, int table_u16, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
   int rcap = 32;
   while (rcap < max_R) rcap <<= 1;
@@ -455,7 +459,7 @@ cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_
 #define CCM_TBLAUNCH(EV)                                                                 \
   if (E == EV) {                                                                         \
     table_build_kernel<EV><<<grid, kTableWarps * 32, table_smem(rcap, staged), s>>>(     \
-        series, jobs, order, table, table_dist, table_tv, table_u16, rcap, staged);        \
+        series, jobs, order, table, table_dist, table_pairs, table_u16, rcap, staged);     \
     return cudaGetLastError();                                                           \
   }
   CCM_FOR_E(CCM_TBLAUNCH)
