@@ -486,17 +486,6 @@ void append_units(const ProblemCopy& pc, int64_t series_off, int64_t out_base, U
   }
 }
 
-// Sort the work list by decreasing cost (longest first), ties by position.
-void sort_by_cost(std::vector<WorkItem>* items, const std::vector<double>& cost) {
-  std::vector<int64_t> order(items->size());
-  for (size_t q = 0; q < order.size(); ++q) order[q] = (int64_t)q;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int64_t a, int64_t b) { return cost[(size_t)a] > cost[(size_t)b]; });
-  std::vector<WorkItem> sorted(order.size());
-  for (size_t q = 0; q < order.size(); ++q) sorted[q] = (*items)[(size_t)order[q]];
-  items->swap(sorted);
-}
-
 void sort_items(UnitList* ul) {
   std::stable_sort(ul->tables.begin(), ul->tables.end(), [](const TableJob& a, const TableJob& b) {
     const int ra = UnitList::table_rcap(a.R), rb = UnitList::table_rcap(b.R);

@@ -61,6 +61,45 @@ def test_table_equals_brute_force_and_oracle(ccm):
     check_units(p, r1, l1, n1, x1, which=set(int(u) for u in rng.choice(r1.size, 12, replace=False)))
 
 
+def rho_only(ccm, ctx, p, flags):
+    plan = ccm.plan_problem(ctx, p, flags)
+    try:
+        rho = np.zeros(ccm.rho_shape(p))
+        ccm.ccm_run(plan, p.series, rho)
+    finally:
+        ccm.ccm_plan_destroy(plan)
+    return rho
+
+
+def test_table_target_values_match_brute_force(ccm):
+    """Without neighbour lists requested, a table of a variable with one target
+    holds (distance, target value) pairs and the scan reads the target's values
+    from it; with several targets per variable it gathers them.  Either way rho
+    is bit-identical to brute force, and to the run that also returns the
+    neighbour lists (which reads the indices)."""
+    base = I.sweep_problem()
+    s = np.ascontiguousarray(base.series[:, :3000])
+    one = I.Problem(series=s, pairs=I.BOTH_DIRECTIONS.copy(), E=np.array([2, 7], np.int32),
+                    tau=np.array([1, 2], np.int32), L=np.array([300, 1400, 2900], np.int64),
+                    r=9, seed=base.seed, name="one-target")
+    s3 = np.ascontiguousarray(np.vstack([s, s[:1] * 0.5 + s[1:] * 0.5]))
+    many = I.Problem(series=s3, pairs=np.array([[0, 1], [0, 2], [1, 0], [2, 1]], np.int32),
+                     E=np.array([3], np.int32), tau=np.array([1], np.int32),
+                     L=np.array([400, 1500, 2900], np.int64), r=9, seed=base.seed,
+                     name="two-targets")
+    ctx = ccm.ccm_context_create(0)
+    try:
+        for p in (one, many):
+            assert uses_table(ccm, ctx, p)
+            brute = rho_only(ccm, ctx, p, ccm.CCM_NO_TABLE)
+            table = rho_only(ccm, ctx, p, 0)
+            detailed = run_detailed(ccm, ctx, p, 0)[0]
+            np.testing.assert_array_equal(table, brute)
+            np.testing.assert_array_equal(table, detailed)
+    finally:
+        ccm.ccm_context_destroy(ctx)
+
+
 def test_table_with_exact_ties_and_full_library(ccm):
     rng = np.random.default_rng(8)
     ints = rng.integers(0, 6, size=(2, 2500)).astype(np.float32)
