@@ -35,6 +35,8 @@
 // sort orders the R keys (bits << 32 | index).
 #include <stdint.h>
 
+#include <initializer_list>
+
 #include "ccm_internal.h"
 
 namespace ccm {
@@ -396,8 +398,12 @@ __device__ void build_row(const float* s, const TableJob& jb, int pos, bool row,
   __syncwarp();
 }
 
-template <int E>
-__global__ void __launch_bounds__(kTableWarps * 32, 2)
+// kMinCtas CTAs per SM: 2 (128 registers) for the exact two-pass build of
+// short manifolds, 3 for the sampled single pass of long ones, whose loads
+// want more warps in flight (measured: the sweep's tables 63 vs 68 ms with 3,
+// the N = 10^5 series' 203 vs 185 ms).
+template <int E, int kMinCtas>
+__global__ void __launch_bounds__(kTableWarps * 32, kMinCtas)
 table_build_kernel(const float* series, const TableJob* jobs, const int32_t* order, void* table,
                    float* table_dist, int pairs, int u16, int rcap, int staged) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -436,10 +442,9 @@ size_t table_smem(int rcap, bool staged) {
 
 cudaError_t table_prepare() {
 #define CCM_TBPREP(EV)                                                                   \
-  {                                                                                      \
+  for (const auto fn : {table_build_kernel<EV, 2>, table_build_kernel<EV, 3>}) {         \
     const cudaError_t e = cudaFuncSetAttribute(                                          \
-        table_build_kernel<EV>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
-        (int)table_smem(kTableMaxR, true));                                              \
+        fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table_smem(kTableMaxR, true)); \
     if (e != cudaSuccess) return e;                                                      \
   }
   CCM_FOR_E(CCM_TBPREP)
@@ -458,8 +463,12 @@ cudaError_t launch_table_build(const float* series, const TableJob* jobs, int64_
   const int staged = (E >= 5 && max_nm >= kSampleMinNm) ? 1 : 0;
 #define CCM_TBLAUNCH(EV)                                                                 \
   if (E == EV) {                                                                         \
-    table_build_kernel<EV><<<grid, kTableWarps * 32, table_smem(rcap, staged), s>>>(     \
-        series, jobs, order, table, table_dist, table_pairs, table_u16, rcap, staged);     \
+    if (max_nm >= kSampleMinNm)                                                          \
+      table_build_kernel<EV, 3><<<grid, kTableWarps * 32, table_smem(rcap, staged), s>>>( \
+          series, jobs, order, table, table_dist, table_pairs, table_u16, rcap, staged);   \
+    else                                                                                 \
+      table_build_kernel<EV, 2><<<grid, kTableWarps * 32, table_smem(rcap, staged), s>>>( \
+          series, jobs, order, table, table_dist, table_pairs, table_u16, rcap, staged);   \
     return cudaGetLastError();                                                           \
   }
   CCM_FOR_E(CCM_TBLAUNCH)
