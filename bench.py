@@ -326,9 +326,10 @@ def check_accuracy(ccm, ctx, p, rho_sweep, kept):
 
 
 # ------------------------------------------------------------ GPU arm ------
-def traffic_entry():
-    """DRAM bytes of the fused kernels per sweep (ten per-E launches) from the
-    committed ncu summary, if the kernel source still matches the profiled one."""
+def ncu_record():
+    """The committed ncu record of the brute-force launches (DRAM bytes per
+    sweep, pipe use of the E = 10 launch), if the kernel source still matches
+    the profiled one."""
     try:
         rec = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
@@ -336,7 +337,21 @@ def traffic_entry():
     h = hashlib.sha256(open(KNN_SRC, "rb").read()).hexdigest()
     if rec.get("knn_fused_sha256") != h or rec.get("path") != "default":
         return None
-    return rec.get("dram_bytes_per_full_sweep")
+    return rec
+
+
+def executed_pairs(ccm, ctx, p, dev_flags, s_dev, rho_dev, stream):
+    """Query-library pairs the brute-force search actually evaluated in one run
+    (the counting variant, CCM_SEARCH_STATS: same results, slower): begun
+    (at least the first coordinates) and completed (all E)."""
+    plan = ccm.plan_problem(ctx, p, dev_flags | ccm.CCM_SEARCH_STATS)
+    try:
+        ccm.ccm_run(plan, s_dev, rho_dev, stream=stream)
+        stream.synchronize()
+        st = ccm.ccm_plan_search_stats(plan)
+    finally:
+        ccm.ccm_plan_destroy(plan)
+    return st["pairs_begun"], st["pairs_full"]
 
 
 def time_steps(ccm, plan, s_dev, rho_dev, stream, flush, steps, warmup, after=None):
@@ -442,8 +457,12 @@ def run_ours(args, rank, world, local_rank, cpu=None):
     if rank == 0:
         n_units = info["n_units"]
         st = mean_stages(stage_ms)
-        # dominant kernel: the brute-force fused kernels (small-L realizations)
+        # roofline: the brute-force fused kernels (small-L realizations), the
+        # search kernel whose work has a compute roofline (the table scan, the
+        # largest stage, is characterised in its own block)
         achieved = info["brute_flop_count"] / (st[2] / 1e3) / 1e12
+        ncu_rec = ncu_record() if args.workload == "sweep" else None
+        ex_begun, ex_full = executed_pairs(ccm, ctx, p, dev_flags, s_dev, rho_dev, stream)
         out = {
             "metric": METRIC, "value": job_throughput(n_units, world, t_step / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -483,7 +502,7 @@ def run_ours(args, rank, world, local_rank, cpu=None):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          # the committed capture covers the sweep workload only
-                         "traffic": traffic_entry() if args.workload == "sweep" else None,
+                         "traffic": (ncu_rec or {}).get("dram_bytes_per_full_sweep"),
                          "traffic_unit": "DRAM bytes per step, all brute-force launches "
                                          "(ncu, scaled from an r=8 capture)",
                          "algorithmic_bytes": "4L per realization (library indices) + 8 (rho)",
@@ -493,6 +512,12 @@ def run_ours(args, rank, world, local_rank, cpu=None):
                                    "method's exhaustive work, including the pairs that exact "
                                    "chunk pruning skips)",
                          "brute_pairs_per_s": info["brute_pair_count"] / (st[2] / 1e3),
+                         # pairs the search evaluated (pruning skips the rest), counted
+                         # by a separate run of the counting variant, per second of the
+                         # timed brute-force stage
+                         "executed_pairs_per_s": ex_begun / (st[2] / 1e3),
+                         "completed_pairs_per_s": ex_full / (st[2] / 1e3),
+                         "ncu_e10_launch": (ncu_rec or {}).get("pipes_e10"),
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "e2e": {"value": job_throughput(n_units, world, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": int(p.series.nbytes) + int(rho_host.nbytes),
