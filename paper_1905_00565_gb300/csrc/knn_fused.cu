@@ -68,7 +68,6 @@ constexpr unsigned kFull = 0xffffffffu;
 //   V = 1 "wide":   early termination for E >= 3 (after 2 coordinates for
 //                   E <= 6, after 3 above), and 8 points per step for E <= 6
 //                   (4 above: registers run out).
-constexpr int kVariants = 2;
 
 // Library points per step (two points per packed operand): more points give
 // more independent FMA chains per warp.
@@ -1155,10 +1154,14 @@ __device__ void process_table_item(const KnnParams& p, int unit0, int count, int
   }
 }
 
-template <int E, bool kStats>
-// Four CTAs per SM (64 registers a thread): the table walk waits on L2, and
-// more resident warps hide more of it than the few spilled registers cost.
-__global__ void __launch_bounds__(kThreads, 4) knn_table_kernel(KnnParams p) {
+// kMinCtas CTAs per SM.  Four (64 registers a thread) for manifolds with a
+// byte map: the walk waits on L2, and more resident warps hide more of it
+// than the few spilled registers cost (the sweep's scan: 151 ms, 165 ms with
+// three).  Three (80 registers) for longer manifolds (bitmap, one realization
+// an item, tables beyond L2), which want the registers (the N = 10^5 series'
+// scan: 110 ms, 120 ms with four).
+template <int E, bool kStats, int kMinCtas>
+__global__ void __launch_bounds__(kThreads, kMinCtas) knn_table_kernel(KnnParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ RingMeta s_meta[kRing];
@@ -1230,7 +1233,8 @@ cudaError_t knn_table_prepare() {
   // the largest bitmap any plan may need (manifolds up to kTableMaxNm points);
   // set once, so that plans of different sizes never lower it for each other
 #define CCM_TPREP(EV)                                                             \
-  for (const auto fn : {knn_table_kernel<EV, false>, knn_table_kernel<EV, true>}) { \
+  for (const auto fn : {knn_table_kernel<EV, false, 4>, knn_table_kernel<EV, true, 4>,  \
+                        knn_table_kernel<EV, false, 3>}) {                          \
     const cudaError_t e = cudaFuncSetAttribute(                                   \
         fn, cudaFuncAttributeMaxDynamicSharedMemorySize,                          \
         (int)knn_table_smem(kTableMaxNm));                                        \
@@ -1241,18 +1245,23 @@ cudaError_t knn_table_prepare() {
   return cudaSuccess;
 }
 
+// Launches whose manifolds exceed the byte map use the three-CTA kernels
+// (the counting variant always the four-CTA ones).
 cudaError_t knn_table_occupancy(int max_nm, int* ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, knn_table_kernel<kMaxE, false>,
-                                                       kThreads, knn_table_smem(max_nm));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      ctas, max_nm > kByteMapMax ? knn_table_kernel<kMaxE, false, 3> : knn_table_kernel<kMaxE, false, 4>,
+      kThreads, knn_table_smem(max_nm));
 }
 
 cudaError_t launch_knn_table(const KnnParams& p, int E, int max_nm, int grid, cudaStream_t s) {
 #define CCM_TLAUNCH(EV)                                                           \
   if (E == EV) {                                                                  \
     if (p.stats)                                                                  \
-      knn_table_kernel<EV, true><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p); \
+      knn_table_kernel<EV, true, 4><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p); \
+    else if (max_nm > kByteMapMax)                                                \
+      knn_table_kernel<EV, false, 3><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p); \
     else                                                                          \
-      knn_table_kernel<EV, false><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p); \
+      knn_table_kernel<EV, false, 4><<<grid, kThreads, knn_table_smem(max_nm), s>>>(p); \
     return cudaGetLastError();                                                    \
   }
   CCM_FOR_E(CCM_TLAUNCH)
