@@ -340,18 +340,18 @@ def ncu_record():
     return rec
 
 
-def executed_pairs(ccm, ctx, p, dev_flags, s_dev, rho_dev, stream):
-    """Query-library pairs the brute-force search actually evaluated in one run
-    (the counting variant, CCM_SEARCH_STATS: same results, slower): begun
-    (at least the first coordinates) and completed (all E)."""
+def search_counts(ccm, ctx, p, dev_flags, s_dev, rho_dev, stream):
+    """Work counts of one run of the counting variant (CCM_SEARCH_STATS: same
+    results, slower): the query-library pairs the brute-force search began
+    (at least the first coordinates) and completed (all E), and the table
+    entries the table walks loaded and the queries that missed."""
     plan = ccm.plan_problem(ctx, p, dev_flags | ccm.CCM_SEARCH_STATS)
     try:
         ccm.ccm_run(plan, s_dev, rho_dev, stream=stream)
         stream.synchronize()
-        st = ccm.ccm_plan_search_stats(plan)
+        return ccm.ccm_plan_search_stats(plan)
     finally:
         ccm.ccm_plan_destroy(plan)
-    return st["pairs_begun"], st["pairs_full"]
 
 
 def time_steps(ccm, plan, s_dev, rho_dev, stream, flush, steps, warmup, after=None):
@@ -462,7 +462,9 @@ def run_ours(args, rank, world, local_rank, cpu=None):
         # largest stage, is characterised in its own block)
         achieved = info["brute_flop_count"] / (st[2] / 1e3) / 1e12
         ncu_rec = ncu_record() if args.workload == "sweep" else None
-        ex_begun, ex_full = executed_pairs(ccm, ctx, p, dev_flags, s_dev, rho_dev, stream)
+        counts = search_counts(ccm, ctx, p, dev_flags, s_dev, rho_dev, stream)
+        ex_begun, ex_full = counts["pairs_begun"], counts["pairs_full"]
+        idx_bytes = 2 if int(p.series.shape[1]) < 65536 else 4
         out = {
             "metric": METRIC, "value": job_throughput(n_units, world, t_step / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -493,6 +495,11 @@ def run_ours(args, rank, world, local_rank, cpu=None):
                           "cell) has E+1 library members, then the simplex/moment epilogue",
                 "share_of_step": st[3] / t_step,
                 "query_realizations_per_s": info["table_query_count"] / (st[3] / 1e3),
+                # from the counting run: rank entries the walks loaded (one walk
+                # serves up to four realizations) and the index bytes they read
+                "entries_loaded_per_s": counts["table_entries"] / (st[3] / 1e3),
+                "index_bytes_per_s": counts["table_entries"] * idx_bytes / (st[3] / 1e3),
+                "library_scan_fallbacks": counts["table_fallbacks"],
                 "brute_force_query_realizations_per_s":
                     (info["search_query_count"] - info["table_query_count"]) / (st[2] / 1e3),
                 "bound": "issue and L2 latency (see the committed ncu summary)"},
