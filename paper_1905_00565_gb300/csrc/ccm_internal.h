@@ -198,7 +198,7 @@ constexpr int32_t kErrBadUnit = 1;
 constexpr int32_t kErrSampler = 2;
 
 // Sampler (sampler.cu).
-constexpr int kSamplerThreads = 512;
+constexpr int kSamplerThreads = 256;
 constexpr int kSamplerSmemKeys = 40960;   // keys kept in shared memory up to this N_m
 cudaError_t sampler_prepare();
 cudaError_t launch_sampler(const SamplerParams& p, int64_t first_unit, int64_t count,
